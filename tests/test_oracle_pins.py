@@ -1,0 +1,301 @@
+"""Pins of the FP64 oracle against results fixed outside it (brute force, Onsager's closed
+form, the high-temperature series, exact linear algebra and symmetry).  CPU only."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ising, philox, rla, trg
+from tests import exact_ising
+
+INF = trg.Params(None, None, q=2)
+
+
+def _dense_site(A, s, B):
+    d = A.ndim - 1
+    Da = s.size
+    T = (A.reshape(-1, Da) * s[None, :]) @ B.reshape(Da, -1)
+    return T.reshape(A.shape[:d] + B.shape[1:])
+
+
+def test_single_site_trace():
+    """P1: the one-site torus is all self-loops: Z = sum_s e^{hs} prod_mu Bm[s, s]."""
+    for d, beta, h in ((4, 0.1497, 0.0), (4, 0.3, 0.2), (2, 0.7, -0.1), (3, 0.2, 0.05)):
+        A, s, B, c0 = ising.initial_state(beta, h, d)
+        got = math.log(c0) + math.log(trg.trace(A, s, B))
+        want = d * beta + math.log(math.exp(h) + math.exp(-h))
+        assert abs(got - want) < 1e-13
+
+
+def test_initial_tensor_bond_weight():
+    """sum_x W[s, x] W[s', x] = exp(beta s s') for both square roots of the bond matrix."""
+    for beta in (0.05, 0.1497, 0.9):
+        Bm = np.array([[math.exp(beta), math.exp(-beta)], [math.exp(-beta), math.exp(beta)]])
+        for W in (ising.w_symmetric(beta), ising.w_paper(beta)):
+            assert np.allclose(W @ W.T, Bm, rtol=1e-14, atol=0)
+    with pytest.raises(ValueError):
+        ising.w_symmetric(0.0)
+
+
+@pytest.mark.parametrize("h", [0.0, 0.13])
+def test_brute_force_4d_2x2x2x2(h):
+    """P5: 2^4 torus (16 spins, 2^16 configurations, 64 bonds with double bonds from L=2).
+    Two untruncated RG steps (directions 1, 2) leave a 1x1x2x2 torus, contracted densely."""
+    beta = 0.1497
+    run = trg.Run(beta, h, 4, INF).step(2)
+    T = _dense_site(run.A, run.s, run.B)          # legs (dir3, dir4, dir1, dir2)^2
+    T2 = np.einsum("abcdefcd->abef", T)           # trace directions 1 and 2 (L = 1)
+    zrem = np.einsum("aebf,bgah,cfde,dhcg->", T2, T2, T2, T2)
+    got = run.partial_lnz() + math.log(zrem) / 16.0
+    want, _, _ = exact_ising.brute_force_lnz(beta, h, (2, 2, 2, 2))
+    assert abs(got - want / 16.0) < 1e-12
+
+
+def test_brute_force_2d_4x4_full_pipeline():
+    """P6: 4x4 torus, four untruncated ATRG steps down to one site (d = 2)."""
+    for beta, h in ((0.3, 0.0), (0.44, 0.07), (0.9, -0.2)):
+        got = trg.Run(beta, h, 2, INF).step(4).lnz()
+        want, _, _ = exact_ising.brute_force_lnz(beta, h, (4, 4))
+        assert abs(got - want / 16.0) < 1e-12, (beta, h, got, want / 16)
+
+
+def test_brute_force_3d_2x2x2():
+    """Untruncated d = 3 pipeline (triad group of one leg) against enumeration."""
+    beta, h = 0.25, 0.05
+    got = trg.Run(beta, h, 3, INF).step(3).lnz()
+    want, _, _ = exact_ising.brute_force_lnz(beta, h, (2, 2, 2))
+    assert abs(got - want / 8.0) < 1e-12
+
+
+def test_internal_energy_and_magnetisation_fd():
+    """P5 (derivatives): central differences of the untruncated ln Z give the brute-force
+    <sum ss> / V and <sum s> / V of the 2^4 torus."""
+    beta, h, e = 0.1497, 0.05, 1e-5
+
+    def lnz(b, hh):
+        run = trg.Run(b, hh, 4, INF).step(2)
+        T = _dense_site(run.A, run.s, run.B)
+        T2 = np.einsum("abcdefcd->abef", T)
+        return run.partial_lnz() + math.log(np.einsum("aebf,bgah,cfde,dhcg->", T2, T2, T2, T2)) / 16
+
+    _, ebond, mag = exact_ising.brute_force_lnz(beta, h, (2, 2, 2, 2))
+    du = (lnz(beta + e, h) - lnz(beta - e, h)) / (2 * e)
+    dm = (lnz(beta, h + e) - lnz(beta, h - e)) / (2 * e)
+    assert abs(du - ebond / 16) < 1e-8
+    assert abs(dm - mag / 16) < 1e-8
+
+
+def test_z2_symmetry_untruncated():
+    """P9: ln Z(h) = ln Z(-h) and d ln Z / dh = 0 at h = 0."""
+    beta = 0.5
+    a = trg.Run(beta, 0.3, 2, INF).step(4).lnz()
+    b = trg.Run(beta, -0.3, 2, INF).step(4).lnz()
+    assert abs(a - b) < 1e-13
+    e = 1e-4
+    m = (trg.Run(beta, e, 2, INF).step(4).lnz() - trg.Run(beta, -e, 2, INF).step(4).lnz()) / (2 * e)
+    assert abs(m) < 1e-9
+
+
+def test_gauge_of_w():
+    """P10: the symmetric square root and the paper's W (square roots restored) differ by an
+    orthogonal gauge on every bond, so untruncated ln Z agrees."""
+    beta, h = 0.35, 0.1
+    a = trg.Run(beta, h, 2, INF).step(4).lnz()
+    b = trg.Run(beta, h, 2, INF, W=ising.w_paper(beta)).step(4).lnz()
+    assert abs(a - b) < 1e-13
+
+
+@pytest.mark.parametrize("beta", [0.3, 0.6])
+def test_onsager_2d(beta):
+    """P7: d = 2 on a 2^20 x 2^20 torus approaches Onsager's infinite-lattice value, and the
+    error shrinks as chi grows."""
+    exact = exact_ising.onsager_lnz(beta)
+    errs = []
+    for chi in (4, 8, 16):
+        p = trg.Params(chi, 3, q=2, seed=7)
+        errs.append(abs(trg.lnz_per_site(beta, 0.0, 2, p, 40) - exact))
+    assert errs[-1] < 1e-7, errs
+    assert errs[-1] < errs[0], errs
+
+
+def test_high_temperature_series_4d():
+    """P8: at beta = 0.015 (2^16 sites, 16 steps) ln 2 + 4 ln cosh b + 6 tanh^4 b holds to
+    O(tanh^6) ~ 1e-9 plus the chi truncation error, which shrinks with chi (single-bond
+    excitations on the block boundary form large multiplets that chi cuts).  At chi = 12 the
+    total error is below 1e-7 while the tanh^4 term is 3e-7, so a wrong plaquette count or a
+    wrong ln cosh coefficient fails."""
+    beta = 0.015
+    series = exact_ising.high_t_lnz(beta, 4)
+    errs = [abs(trg.lnz_per_site(beta, 0.0, 4, trg.Params(chi, 2, q=2, seed=3), 16) - series)
+            for chi in (4, 12)]
+    assert errs[1] < 1e-7, errs
+    assert errs[1] < errs[0], errs
+
+
+def test_exact_triad_reproduces_unit_cell():
+    """P3 / Eq. 4: with r chi >= the grouped dimension the triad network equals Gamma."""
+    run = trg.Run(0.1497, 0.02, 4, trg.Params(6, 2, seed=5)).step(2)
+    A, s, B = run.A, run.s, run.B
+    p = trg.Params(64, 64, seed=5)
+    X, sig, Y = trg.bond_swap(A, s, B, p, 3)
+    E, F, G, H, I, J, K, L = trg.triad(A, B, X, sig, Y, p, 3)
+    # Gamma = A X sigma Y D with all legs open; compare the forward half A X sigma
+    gam = np.einsum("iabsx,xcdtg,g->iabscdtg", A, X, sig)
+    tri = np.einsum("iksx,abk,xlth,cdl->iabscdth", E, I, F, J)
+    assert np.allclose(gam, tri, atol=1e-13 * np.abs(gam).max())
+    gam_b = np.einsum("ybcdg,jefhy->bcdgjefh", Y, np.moveaxis(B, 0, -1))
+    tri_b = np.einsum("ykdg,bck,jlhy,efl->bcdgjefh", G, K, H, L)
+    assert np.allclose(gam_b, tri_b, atol=1e-13 * np.abs(gam_b).max())
+
+
+def test_truncated_isometry_error_is_dropped_weight():
+    """Eq. 2: ||Gamma - U U^T Gamma||^2 on A's grouped legs equals the discarded eigenvalue
+    weight of rho_A when U holds exact leading eigenvectors."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((3, 4, 4, 3, 5))
+    Xi = rng.standard_normal((5, 5))
+    Xi = Xi @ Xi.T
+    L = np.linalg.cholesky(Xi)
+    AX = np.einsum("iabsx,xy->iabsy", A, L)          # Gamma restricted: A times a square root of Xi
+    M = np.transpose(AX, (1, 2, 0, 3, 4)).reshape(16, -1)
+    rho = M @ M.T
+    lam, U = rla.eigh_desc(rho)
+    k = 6
+    Uk = U[:, :k]
+    err = np.linalg.norm(M - Uk @ (Uk.T @ M)) ** 2
+    assert abs(err - lam[k:].sum()) < 1e-10 * lam.sum()
+
+
+def test_triad_with_full_width_equals_atrg():
+    """P4: r = chi makes Triad-ATRG identical to ATRG with the same sketches."""
+    for d in (3, 4):
+        a = trg.lnz_per_site(0.1497, 0.0, d, trg.Params(4, 4, seed=2, method="triad"), 6)
+        b = trg.lnz_per_site(0.1497, 0.0, d, trg.Params(4, 4, seed=2, method="atrg"), 6)
+        assert abs(a - b) < 1e-12, (d, a, b)
+
+
+def test_truncation_error_shrinks_with_chi_4d():
+    """P5 (truncated): on the 2^4 torus the error of chi = 4, 6, 8 runs shrinks."""
+    beta, h = 0.1497, 0.0
+    want, _, _ = exact_ising.brute_force_lnz(beta, h, (2, 2, 2, 2))
+    errs = []
+    for chi in (2, 4, 8):
+        run = trg.Run(beta, h, 4, trg.Params(chi, 2, seed=1)).step(2)
+        T = _dense_site(run.A, run.s, run.B)
+        T2 = np.einsum("abcdefcd->abef", T)
+        z = np.einsum("aebf,bgah,cfde,dhcg->", T2, T2, T2, T2)
+        errs.append(abs(run.partial_lnz() + math.log(z) / 16 - want / 16))
+    assert errs[2] < errs[0]
+
+
+# --- randomized linear algebra --------------------------------------------------------
+
+def _test_matrix(m, n, decay, seed):
+    rng = np.random.default_rng(seed)
+    U, _ = np.linalg.qr(rng.standard_normal((m, min(m, n))))
+    V, _ = np.linalg.qr(rng.standard_normal((n, min(m, n))))
+    S = decay ** np.arange(min(m, n))
+    return (U * S) @ V.T, S
+
+
+def test_orth_properties():
+    rng = np.random.default_rng(0)
+    Y = rng.standard_normal((200, 17))
+    Q, R = rla.orth(Y)
+    assert np.allclose(Q.T @ Q, np.eye(17), atol=1e-14)
+    assert np.allclose(Q @ R, Y, atol=1e-13)
+    assert np.all(np.diag(R) >= 0) and np.allclose(R, np.triu(R))
+
+
+def test_rsvd_full_width_is_exact():
+    """P11: ell >= min(m, n) recovers the exact SVD."""
+    M, S = _test_matrix(60, 40, 0.7, 1)
+    om = philox.gaussian(1, 5, 40, 40)
+    U, s, V = rla.rsvd(rla.DenseOp(M), 40, 1, om)
+    assert np.allclose(s, S, rtol=1e-10, atol=1e-14)
+    assert np.allclose((U * s) @ V.T, M, atol=1e-13)
+
+
+def test_rsvd_error_decreases_with_q():
+    """P11: the rank-k error of the randomized SVD approaches sigma_{k+1} as q grows."""
+    M, S = _test_matrix(300, 200, 0.93, 2)
+    k, ell = 20, 30
+    om = philox.gaussian(3, 9, 200, ell)
+    errs = []
+    for q in (0, 1, 2):
+        U, s, V = rla.rsvd(rla.DenseOp(M), ell, q, om)
+        errs.append(np.linalg.norm(M - (U[:, :k] * s[:k]) @ V[:, :k].T, 2))
+    assert errs[0] > errs[1] > errs[2] >= S[k] * (1 - 1e-12)
+    assert errs[2] < 1.05 * S[k]
+
+
+def test_rsvd_psd_matches_eigh():
+    M, S = _test_matrix(80, 80, 0.9, 4)
+    rho = M @ M.T
+    om = philox.gaussian(3, 10, 80, 80)
+    lam, U = rla.rsvd_psd(lambda x: rho @ x, 80, 1, om)
+    assert np.allclose(lam, S ** 2, rtol=1e-9, atol=1e-15)
+
+
+def test_sign_convention():
+    rng = np.random.default_rng(5)
+    V = rng.standard_normal((50, 7))
+    W, sgn = rla.fix_sign(V)
+    w = rla.sign_weights(50)
+    assert np.all(w @ W > 0)
+    W2, _ = rla.fix_sign(-V)
+    assert np.array_equal(W, W2)
+
+
+# --- Philox sketch stream -------------------------------------------------------------
+
+def test_philox_gaussian_statistics():
+    """N(0,1) moments, uniformity of the 53-bit uniforms and independence of the pair."""
+    z = philox.gaussian(1234, philox.stream_id(3, 0), 1000, 1000)
+    x = z.ravel()
+    assert abs(x.mean()) < 5e-3
+    assert abs(x.var() - 1) < 5e-3
+    assert abs(np.mean(x ** 4) - 3) < 3e-2
+    assert abs(np.corrcoef(x[0::2], x[1::2])[0, 1]) < 5e-3
+    w0, w1, w2, w3 = philox.philox_words(1234, 77, 0, 200000)
+    u = np.sort(np.concatenate([philox._uniform53(w0, w1), philox._uniform53(w2, w3)]))
+    assert u[0] > 0 and u[-1] < 1
+    ks = np.max(np.abs(u - (np.arange(1, u.size + 1) - 0.5) / u.size))
+    assert ks < 1.63 / math.sqrt(u.size) * 1.5
+
+
+def test_philox_stream_layout():
+    """Element e uses counter pair e // 2 and takes z_{e mod 2}; streams and replicas differ."""
+    a = philox.gaussian(9, 5, 3, 7).ravel()
+    b = philox.gaussian(9, 5, 1, 21).ravel()
+    assert np.array_equal(a, b)
+    c = philox.gaussian(9, 6, 3, 7).ravel()
+    r = philox.gaussian(9, 5, 3, 7, replica=1).ravel()
+    assert not np.any(a == c) and not np.any(a == r)
+    w0, w1, w2, w3 = philox.philox_words(9, 5, 5, 1)
+    u1 = philox._uniform53(w0, w1)[0]
+    u2 = philox._uniform53(w2, w3)[0]
+    assert a[10] == math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2)
+    assert a[11] == math.sqrt(-2 * math.log(u1)) * math.sin(2 * math.pi * u2)
+
+
+def test_philox_is_a_bijection_on_small_counters():
+    """Distinct counters give distinct outputs (Philox is a keyed bijection)."""
+    w = philox.philox_words(0, 0, 0, 1 << 16)
+    packed = set(zip(*[x.tolist() for x in w]))
+    assert len(packed) == 1 << 16
+
+
+def test_flop_counts_match_cost_formulas():
+    """P13 / Table 1: at steady state (every leg chi, triad width r chi) one step counts
+    (2q+2) 4 r chi^7 swap flops and 8 r^2 chi^7 + O(r^2 chi^6) contraction flops."""
+    chi, r, q = 4, 2, 2
+    run = trg.Run(0.1497, 0.0, 4, trg.Params(chi, r, q=q, seed=1)).step(4)
+    before = dict(run.cnt.flops)
+    run.step()
+    assert run.A.shape == (chi,) * 5
+    delta = {k: run.cnt.flops[k] - before[k] for k in before}
+    assert delta["swap"] == (2 * q + 2) * 4 * r * chi ** 7
+    main = 8 * r * r * chi ** 7
+    lower = 4 * r * chi ** 6 + 2 * (2 * r * chi ** 5 + 2 * r * chi ** 6 + 2 * r * r * chi ** 6)
+    assert delta["contract"] == main + lower
