@@ -1,0 +1,179 @@
+/*
+ * tatrg.h -- C ABI of the GB300 (sm_103a) Triad-ATRG library.
+ *
+ * The library coarse-grains the d-dimensional Ising partition function
+ * Z = tTr prod_n T(n) (Sugimoto & Sasaki, arXiv:2412.14104, Sec. 3) with the Triad-ATRG
+ * step of Sec. 2: the bond swap of Eq. 1 truncated by a randomized SVD, the oversampled
+ * triad isometries and tensors of Eqs. 2-4, the squeezers of Eq. 5 and the O(r^2 chi^7)
+ * contraction of Eqs. 6-7, followed by a re-split and normalisation.  Every stage runs in
+ * the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by all entry points
+ *  - Status codes only; nothing throws across this boundary.  On an error the context
+ *    keeps the message returned by tatrg_last_error().
+ *  - "host" pointers are caller-owned CPU memory, read or written before the call returns.
+ *    "device" pointers are caller-owned GPU memory on the current device; the call only
+ *    enqueues work on the given stream unless it says it synchronises.
+ *  - Tensors are dense row-major float64.  A site tensor is stored split as
+ *    T[f; b] = sum_a A[f, a] s[a] B[a, b]: A has shape (D_0, ..., D_{d-1}, Da), s has Da
+ *    entries, B has shape (Da, D_0, ..., D_{d-1}).  Leg position 0 is the direction the
+ *    next step coarse-grains; after a step the leg order rotates left by one.
+ *  - One context per host thread; a context is bound to the device current at creation.
+ */
+#ifndef TATRG_H
+#define TATRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tatrg_ctx tatrg_ctx; /* opaque, library-owned */
+
+typedef enum {
+  TATRG_OK = 0,
+  TATRG_EINVAL = 1,   /* bad argument (sizes, null pointer, unsupported d or precision) */
+  TATRG_ENOMEM = 2,   /* device allocation failed */
+  TATRG_ECUDA = 3,    /* a CUDA runtime or driver call failed */
+  TATRG_ENUMERIC = 4, /* non-finite value, zero norm or non-convergent small solver */
+  TATRG_ETIMEOUT = 5, /* a bounded device-side wait ran out */
+  TATRG_ESTATE = 6,   /* calls in the wrong order (e.g. a step before init) */
+  TATRG_ENOTIMPL = 7  /* the requested feature is not built */
+} tatrg_status;
+
+typedef enum { TATRG_ATRG = 0, TATRG_TRIAD = 1 } tatrg_method;
+
+/* Arithmetic of the large contractions.  QR / SVD / eigen cores and ln Z stay float64. */
+typedef enum {
+  TATRG_FP64 = 0,   /* float64 CUDA-core GEMMs */
+  TATRG_TF32X3 = 1, /* tcgen05 kind::tf32, operands split hi+lo, 3 products, FP32 accumulate */
+  TATRG_BF16X3 = 2  /* tcgen05 kind::f16 with bf16 hi+lo split, 3 products, FP32 accumulate */
+} tatrg_precision;
+
+typedef struct {
+  int chi;        /* bond dimension (Sec. 2; Table 2 uses 38..54) */
+  int r;          /* internal-line oversampling: triad lines carry r*chi (Fig. 1) */
+  int q;          /* power iterations of every randomized SVD (Table 1) */
+  int method;     /* tatrg_method */
+  int precision;  /* tatrg_precision */
+  unsigned long long seed; /* Philox key of all Gaussian sketches */
+  int checkpoint_every;    /* steps between checkpoints of the reverse sweep (0: 4) */
+  int split_from_step;     /* steps before this one run in FP64 whatever the precision */
+} tatrg_params;
+
+/* Create a context on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * The context owns every device buffer it uses (stream-ordered allocations on that
+ * stream).  Fails with EINVAL when chi < 1, r < 1, q < 0, or an enum is out of range. */
+tatrg_status tatrg_create(const tatrg_params* params, void* cuda_stream, tatrg_ctx** out);
+
+/* Build the Ising initial tensor of Sec. 3, T = sum_s e^{hs} prod_mu W[s,x_mu] W[s,x'_mu]
+ * with W the symmetric square root of [[e^b, e^-b], [e^-b, e^b]] (the printed W without
+ * its square roots is read as this), normalise it by its Frobenius norm c_0 and split it
+ * exactly into A s B on the device.  d in {2, 3, 4}; beta > 0.  Resets the step count and
+ * the ln Z accumulator to ln c_0.  Synchronises the context stream. */
+tatrg_status tatrg_init_ising(tatrg_ctx* ctx, double beta, double h, int d);
+
+/* Run `nsteps` coarse-graining steps (Sec. 2, Eqs. 1-7).  Each step halves the lattice
+ * along the leg at position 0, normalises the new tensor by c_k = ||s'||_2 and adds
+ * 2^-k ln c_k to the accumulator.  Returns after the last step's small host reads
+ * (spectra needed for the rank cuts), so the call synchronises the stream. */
+tatrg_status tatrg_rg_step(tatrg_ctx* ctx, int nsteps);
+
+/* ln Z / V after the steps run so far: sum_k 2^-k ln c_k + 2^-N ln tTr T_N, where tTr
+ * traces every forward leg with its own backward leg (a periodic lattice of 2^N sites).
+ * Writes one double to a host pointer.  Synchronises. */
+tatrg_status tatrg_lnZ(tatrg_ctx* ctx, double* lnZ_per_site);
+
+/* Derivatives of ln Z / V with respect to beta and h (internal energy, magnetisation,
+ * and optionally the second beta derivative for the specific heat).  Not built in this
+ * version: returns TATRG_ENOTIMPL. */
+tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh,
+                        double* d2lnZ_dbeta2 /* nullable */);
+
+/* Independent runs over `nbeta` temperatures (host array `betas`), each `nsteps` steps
+ * with the sketch replica index equal to its position in the array; writes ln Z / V for
+ * each to the host array `lnZ_out`.  The context's own state is left untouched. */
+tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double h, int d,
+                         int nsteps, double* lnZ_out);
+
+/* Spectra of the last step, copied to a host array of capacity *n (on return *n holds
+ * the count).  kind: 0 = s' (normalised, re-split), 1 = sigma of the bond swap,
+ * 2 + (nu-1) = squeezer singular values of transverse leg position nu (1..d-1). */
+tatrg_status tatrg_spectrum(const tatrg_ctx* ctx, int kind, double* out, int* n);
+
+/* Copy the current state to host memory.  dims receives d+1 ints (D_0..D_{d-1}, Da);
+ * *d receives d; A, s, B may be NULL to query the sizes only. */
+tatrg_status tatrg_get_state(const tatrg_ctx* ctx, int* d, int* dims, double* A, double* s,
+                             double* B);
+
+/* Replace the state by host tensors (same layout as tatrg_get_state), with `step` steps
+ * already taken and `partial_lnz` = sum_k 2^-k ln c_k so far.  Synchronises. */
+tatrg_status tatrg_set_state(tatrg_ctx* ctx, int d, const int* dims, const double* A,
+                             const double* s, const double* B, int step, double partial_lnz);
+
+/* Per-stage record of the last step (host struct). */
+typedef struct {
+  int step;            /* 1-based index of the step */
+  int dims[5];         /* leg dims D_0..D_3 and Da after the step (unused legs = 0) */
+  int swap_exact;      /* 1 when the swap used the exact SVD */
+  double lnc;          /* ln c_k */
+  double flops[5];     /* algorithmic flops: swap, triad, squeeze, contract, resplit */
+  double ms[5];        /* device time of each stage (CUDA events) */
+  double swap_gap;     /* (sigma_{Dg-1} - sigma_Dg) / sigma_0 at the swap cut (inf if none) */
+  int tc_launches;     /* tcgen05 GEMM launches in the step */
+  int kernel_launches; /* all library kernel launches in the step */
+} tatrg_step_info;
+
+tatrg_status tatrg_last_step_info(const tatrg_ctx* ctx, tatrg_step_info* out);
+
+const char* tatrg_last_error(const tatrg_ctx* ctx);
+void tatrg_destroy(tatrg_ctx* ctx);
+
+/* ---------------------------------------------------------------------------------
+ * Building blocks, exposed for parity tests and for callers that compose their own
+ * networks.  All pointers are device pointers; work is enqueued on `cuda_stream`.
+ * Errors of these calls are reported through tatrg_last_error(NULL).
+ * --------------------------------------------------------------------------------- */
+
+/* Gaussian sketch used by every randomized SVD (Table 1: RSVD with q iterations): element
+ * e of the row-major rows x cols output is z_{e mod 2} of the Box-Muller pair made from
+ * Philox4x32-10 with counter (lo32(e/2), hi32(e/2), replica, hi32(seed)) and key
+ * (lo32(seed), stream_id).  Writes rows*cols doubles to `out`. */
+tatrg_status tatrg_gaussian(unsigned long long seed, uint32_t stream_id, uint32_t replica,
+                            int64_t rows, int64_t cols, double* out, void* cuda_stream);
+
+/* A tensor contraction C[m, n] = alpha sum_k A[m, k] B[k, n] + beta C[m, n] whose m, n
+ * and k are each up to 4 modes with their own element strides (this is how the
+ * contractions of Eqs. 1-7 are expressed without transposes).  Mode i of m has extent
+ * m_ext[i], stride m_sA[i] in A and m_sC[i] in C; modes are listed outermost first and
+ * unused ones have extent 1.  precision selects the FP64 or a split tensor-core path. */
+typedef struct {
+  int64_t m_ext[4], m_sA[4], m_sC[4];
+  int64_t n_ext[4], n_sB[4], n_sC[4];
+  int64_t k_ext[4], k_sA[4], k_sB[4];
+  double alpha, beta;
+} tatrg_contraction;
+
+tatrg_status tatrg_contract(const tatrg_contraction* c, int precision, const double* A,
+                            const double* B, double* C, void* cuda_stream);
+
+/* Orthonormal basis of the columns of the row-major m x n matrix Y (m >= n): Y = Q R with
+ * Q^T Q = 1 and R upper triangular with a non-negative diagonal when Y has full column
+ * rank (CholeskyQR2 with shift); a rank-deficient Y returns k < n columns spanning its
+ * range and R of shape k x n.  Q must hold m*n doubles, R n*n.  *k (host) receives the
+ * column count.  Synchronises the stream. */
+tatrg_status tatrg_orth(int precision, int64_t m, int64_t n, const double* Y, double* Q,
+                        double* R, int* k, void* cuda_stream);
+
+/* Thin SVD of a row-major m x n matrix (m >= n, n <= 1024) by one-sided Jacobi:
+ * A = U diag(S) V^T with S descending.  U: m x n, S: n, V: n x n (row-major, columns are
+ * the right singular vectors).  Synchronises the stream. */
+tatrg_status tatrg_svd(int64_t m, int64_t n, const double* A, double* U, double* S, double* V,
+                       void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TATRG_H */

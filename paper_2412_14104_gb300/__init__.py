@@ -1,0 +1,226 @@
+"""Python binding of libtatrg (GB300 Triad-ATRG).  Argument marshalling only: every step
+of the coarse-graining runs in the library's CUDA kernels.  PyTorch supplies device memory
+and streams for the building-block calls.
+
+The library must have been built (``python -m paper_2412_14104_gb300.build``); importing
+the binding without it raises, there is no fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtatrg.so")
+
+FP64, TF32X3, BF16X3 = 0, 1, 2
+ATRG, TRIAD = 0, 1
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ETIMEOUT",
+           6: "ESTATE", 7: "ENOTIMPL"}
+
+
+class TatrgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (_STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("chi", ctypes.c_int), ("r", ctypes.c_int), ("q", ctypes.c_int),
+                ("method", ctypes.c_int), ("precision", ctypes.c_int),
+                ("seed", ctypes.c_ulonglong), ("checkpoint_every", ctypes.c_int),
+                ("split_from_step", ctypes.c_int)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int), ("dims", ctypes.c_int * 5), ("swap_exact", ctypes.c_int),
+                ("lnc", ctypes.c_double), ("flops", ctypes.c_double * 5),
+                ("ms", ctypes.c_double * 5), ("swap_gap", ctypes.c_double),
+                ("tc_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+
+
+class Contraction(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64 * 4) for n in
+                ("m_ext", "m_sA", "m_sC", "n_ext", "n_sB", "n_sC", "k_ext", "k_sA", "k_sB")] + \
+               [("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libtatrg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtatrg.so is not built; run python -m paper_2412_14104_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        P, D, I, I64, U64, U32 = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                  ctypes.c_int64, ctypes.c_ulonglong, ctypes.c_uint32)
+        sig = {
+            "tatrg_create": [ctypes.POINTER(Params), P, ctypes.POINTER(P)],
+            "tatrg_init_ising": [P, ctypes.c_double, ctypes.c_double, I],
+            "tatrg_rg_step": [P, I],
+            "tatrg_lnZ": [P, D],
+            "tatrg_grad": [P, D, D, D],
+            "tatrg_sweep": [P, D, I, ctypes.c_double, I, I, D],
+            "tatrg_spectrum": [P, I, D, ctypes.POINTER(I)],
+            "tatrg_get_state": [P, ctypes.POINTER(I), ctypes.POINTER(I), D, D, D],
+            "tatrg_set_state": [P, I, ctypes.POINTER(I), D, D, D, I, ctypes.c_double],
+            "tatrg_last_step_info": [P, ctypes.POINTER(StepInfo)],
+            "tatrg_gaussian": [U64, U32, U32, I64, I64, P, P],
+            "tatrg_contract": [ctypes.POINTER(Contraction), I, P, P, P, P],
+            "tatrg_orth": [I, I64, I64, P, P, P, ctypes.POINTER(I), P],
+            "tatrg_svd": [I64, I64, P, P, P, P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.tatrg_last_error.argtypes = [P]
+        L.tatrg_last_error.restype = ctypes.c_char_p
+        L.tatrg_destroy.argtypes = [P]
+        L.tatrg_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(code, ctx=None):
+    if code != 0:
+        msg = lib().tatrg_last_error(ctx)
+        raise TatrgError(code, msg.decode() if msg else "")
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One RG run on the current CUDA device (tatrg_ctx)."""
+
+    def __init__(self, chi, r, q=2, method=TRIAD, precision=FP64, seed=0, split_from_step=0,
+                 stream=None):
+        self.params = Params(chi, r, q, method, precision, seed, 4, split_from_step)
+        h = ctypes.c_void_p()
+        _check(lib().tatrg_create(ctypes.byref(self.params), _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if self._h:
+            lib().tatrg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_ising(self, beta, h, d):
+        _check(lib().tatrg_init_ising(self._h, beta, h, d), self._h)
+        return self
+
+    def rg_step(self, n=1):
+        _check(lib().tatrg_rg_step(self._h, n), self._h)
+        return self
+
+    def lnZ(self):
+        out = ctypes.c_double()
+        _check(lib().tatrg_lnZ(self._h, ctypes.byref(out)), self._h)
+        return out.value
+
+    def grad(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(lib().tatrg_grad(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), self._h)
+        return a.value, b.value, c.value
+
+    def sweep(self, betas, h, d, nsteps):
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        out = np.empty_like(b)
+        _check(lib().tatrg_sweep(self._h, _dptr(b), b.size, h, d, nsteps, _dptr(out)), self._h)
+        return out
+
+    def spectrum(self, kind):
+        n = ctypes.c_int(0)
+        _check(lib().tatrg_spectrum(self._h, kind, None, ctypes.byref(n)), self._h)
+        out = np.empty(max(n.value, 1))
+        _check(lib().tatrg_spectrum(self._h, kind, _dptr(out), ctypes.byref(n)), self._h)
+        return out[:n.value]
+
+    def get_state(self):
+        d = ctypes.c_int()
+        dims = (ctypes.c_int * 5)()
+        _check(lib().tatrg_get_state(self._h, ctypes.byref(d), dims, None, None, None), self._h)
+        dd = d.value
+        D = [dims[i] for i in range(dd)]
+        Da = dims[dd]
+        A = np.empty(tuple(D) + (Da,))
+        B = np.empty((Da,) + tuple(D))
+        s = np.empty(Da)
+        _check(lib().tatrg_get_state(self._h, ctypes.byref(d), dims, _dptr(A), _dptr(s), _dptr(B)), self._h)
+        return A, s, B
+
+    def set_state(self, A, s, B, step, partial_lnz):
+        d = A.ndim - 1
+        dims = (ctypes.c_int * 5)(*(list(A.shape[:d]) + [s.size] + [0] * (4 - d)))
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        s = np.ascontiguousarray(s, dtype=np.float64)
+        _check(lib().tatrg_set_state(self._h, d, dims, _dptr(A), _dptr(s), _dptr(B), step,
+                                     partial_lnz), self._h)
+        return self
+
+    def step_info(self):
+        info = StepInfo()
+        _check(lib().tatrg_last_step_info(self._h, ctypes.byref(info)), self._h)
+        return info
+
+
+# --- building blocks on torch CUDA tensors --------------------------------------------
+
+def gaussian(seed, stream_id, rows, cols, out, replica=0, stream=None):
+    assert out.is_cuda and out.numel() >= rows * cols
+    _check(lib().tatrg_gaussian(seed, stream_id, replica, rows, cols,
+                                ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def contract(m, n, k, A, B, C, alpha=1.0, beta=0.0, precision=FP64, stream=None):
+    """C[m, n] = alpha sum_k A[m, k] B[k, n] + beta C; m = [(ext, strideA, strideC), ...],
+    n = [(ext, strideB, strideC), ...], k = [(ext, strideA, strideB), ...] (outermost first)."""
+    c = Contraction()
+    for name, modes in (("m", m), ("n", n), ("k", k)):
+        assert len(modes) <= 4
+        full = list(modes) + [(1, 0, 0)] * (4 - len(modes))
+        s1, s2 = {"m": ("m_sA", "m_sC"), "n": ("n_sB", "n_sC"), "k": ("k_sA", "k_sB")}[name]
+        for i, (e, a, b) in enumerate(full):
+            getattr(c, name + "_ext")[i] = e
+            getattr(c, s1)[i] = a
+            getattr(c, s2)[i] = b
+    c.alpha, c.beta = alpha, beta
+    _check(lib().tatrg_contract(ctypes.byref(c), precision, ctypes.c_void_p(A.data_ptr()),
+                                ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
+                                _stream_ptr(stream)))
+    return C
+
+
+def orth(Y, Q, R, precision=FP64, stream=None):
+    m, n = Y.shape
+    k = ctypes.c_int()
+    _check(lib().tatrg_orth(precision, m, n, ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(Q.data_ptr()),
+                            ctypes.c_void_p(R.data_ptr()), ctypes.byref(k), _stream_ptr(stream)))
+    return k.value
+
+
+def svd(A, U, S, V, stream=None):
+    m, n = A.shape
+    _check(lib().tatrg_svd(m, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                           ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                           _stream_ptr(stream)))

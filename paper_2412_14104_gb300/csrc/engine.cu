@@ -1,0 +1,260 @@
+#include "engine.cuh"
+
+#include <cmath>
+
+namespace tatrg {
+
+int keep_count(const std::vector<double>& v, double rel, int64_t cap) {
+  if (v.empty() || !(v[0] > 0.0)) return 0;
+  int64_t n = 0;
+  for (double x : v) n += (x > rel * v[0]) ? 1 : 0;
+  if (cap > 0) n = std::min(n, cap);
+  return int(n);
+}
+
+void Engine::gemm(const GemmDesc& d, const double* A, const double* B, double* C) {
+  const double M = double(d.m.total()), N = double(d.n.total()), K = double(d.k.total());
+  // Tensor cores for the large contractions of the split forms; the FP64 CUDA-core
+  // kernel for everything small (where 128-row tiles would be mostly padding).
+  if (prec != 0 && allow_tc && tc_available() && M * N * K >= 2.0e7 && M >= 32 && N >= 16 &&
+      K >= 16) {
+    gemm_tc(d, A, B, C, prec, s_, &st_);
+  } else {
+    gemm_f64(d, A, B, C, s_, &st_);
+  }
+}
+
+void Engine::mm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta,
+                const double* B, int64_t ldb, bool tb, double* C, int64_t ldc, double alpha,
+                double beta) {
+  GemmDesc g;
+  g.m = modes({{M, ta ? 1 : lda, ldc}});
+  g.n = modes({{N, tb ? ldb : 1, 1}});
+  g.k = modes({{K, ta ? lda : 1, tb ? 1 : ldb}});
+  g.alpha = alpha;
+  g.beta = beta;
+  gemm(g, A, B, C);
+}
+
+std::vector<double> Engine::to_host(const double* p, int64_t n) {
+  std::vector<double> h(size_t(std::max<int64_t>(n, 0)));
+  if (n > 0) TATRG_CUDA(cudaMemcpyAsync(h.data(), p, n * sizeof(double), cudaMemcpyDeviceToHost, s_));
+  TATRG_CUDA(cudaStreamSynchronize(s_));
+  return h;
+}
+
+int Engine::read_flag(int idx) {
+  int v = 0;
+  TATRG_CUDA(cudaMemcpyAsync(&v, flag_.as<int>() + idx, sizeof(int), cudaMemcpyDeviceToHost, s_));
+  TATRG_CUDA(cudaStreamSynchronize(s_));
+  return v;
+}
+
+// CholeskyQR2 (Yamamoto et al. 2015), optionally with a shifted first pass (shifted
+// CholeskyQR3, Fukaya et al. 2020): Q = Y R^-1, R = R2 R1.  ok = false on breakdown.
+OrthResult Engine::cholqr2(const double* Y, int64_t m, int64_t n, double shift, bool& ok) {
+  OrthResult out;
+  const int passes = shift > 0.0 ? 3 : 2;
+  DevBuf G(n * n * sizeof(double), s_), Rk(n * n * sizeof(double), s_),
+      Ri(n * n * sizeof(double), s_), Racc(n * n * sizeof(double), s_),
+      Rtmp(n * n * sizeof(double), s_);
+  DMat cur;
+  const double* src = Y;
+  for (int pass = 0; pass < passes; ++pass) {
+    mm(n, n, m, src, n, true, src, n, false, G.d(), n);
+    cholesky(G.d(), int(n), Rk.d(), flag(0), pass == 0 ? shift : 0.0, s_);
+    st_.launches++;
+    if (read_flag(0) != 0) { ok = false; return out; }
+    tri_inverse(Rk.d(), int(n), Ri.d(), s_);
+    st_.launches++;
+    DMat nxt;
+    nxt.buf = dalloc(m * n, s_);
+    nxt.rows = m;
+    nxt.cols = n;
+    mm(m, n, n, src, n, false, Ri.d(), n, false, nxt.p(), n);
+    if (pass == 0) {
+      TATRG_CUDA(cudaMemcpyAsync(Racc.d(), Rk.d(), n * n * sizeof(double), cudaMemcpyDeviceToDevice, s_));
+    } else {
+      mm(n, n, n, Rk.d(), n, false, Racc.d(), n, false, Rtmp.d(), n);
+      std::swap(Racc, Rtmp);
+    }
+    cur = std::move(nxt);
+    src = cur.p();
+  }
+  ok = true;
+  out.Q = std::move(cur);
+  out.R.buf = std::move(Racc);
+  out.R.rows = n;
+  out.R.cols = n;
+  out.k = int(n);
+  return out;
+}
+
+OrthResult Engine::orth(const double* Y, int64_t m, int64_t n) {
+  TATRG_CHECK(n >= 1, TATRG_EINVAL, "orth: empty matrix");
+  bool ok = false;
+  OrthResult r;
+  if (m >= n) {
+    // FP64 Grams: plain CholeskyQR2.  Split-precision Grams carry ~1e-7 relative error, so
+    // their first pass is shifted (shifted CholeskyQR3).
+    r = cholqr2(Y, m, n, prec == 0 ? 0.0 : 1e-6, ok);
+    if (ok) return r;
+  }
+  // Rank-revealing fallback: eigen-decomposition of the Gram, drop directions whose
+  // eigenvalue is below the relative cut, whiten, then CholeskyQR2 on the whitened basis.
+  DevBuf G(n * n * sizeof(double), s_);
+  mm(n, n, m, Y, n, true, Y, n, false, G.d(), n);
+  SvdResult e = svd(G.d(), n, n);
+  const double cut = prec == 0 ? 1e-14 : 1e-6;
+  int k = keep_count(e.s, cut, std::min<int64_t>(m, n));
+  TATRG_CHECK(k >= 1, TATRG_ENUMERIC, "orth: zero matrix");
+  // W = V_k diag(lambda^-1/2)  (n x k)
+  DMat W;
+  W.buf = dalloc(n * k, s_);
+  W.rows = n;
+  W.cols = k;
+  {
+    ModeIdx cp = modes({{n, e.r, k}, {k, 1, 1}});
+    copy_modes(W.p(), e.V.p(), cp, 1.0, s_);
+    scale_axis(W.p(), e.S.d(), n, k, 1, -2, s_);
+  }
+  DMat Y1;
+  Y1.buf = dalloc(m * k, s_);
+  Y1.rows = m;
+  Y1.cols = k;
+  mm(m, k, n, Y, n, false, W.p(), k, false, Y1.p(), k);
+  int saved = prec;
+  prec = 0;  // the whitened basis is refined in FP64
+  OrthResult q = cholqr2(Y1.p(), m, k, 0.0, ok);
+  prec = saved;
+  TATRG_CHECK(ok, TATRG_ENUMERIC, "orth: CholeskyQR2 failed on the whitened basis");
+  // R = Rq diag(lambda^1/2) V_k^T  (k x n)
+  DMat Vt;
+  Vt.buf = dalloc(int64_t(k) * n, s_);
+  {
+    ModeIdx cp = modes({{k, 1, n}, {n, e.r, 1}});  // Vt[j, i] = V[i, j]
+    copy_modes(Vt.p(), e.V.p(), cp, 1.0, s_);
+    std::vector<double> sq(e.s.begin(), e.s.begin() + k);
+    for (auto& x : sq) x = std::sqrt(x);
+    DevBuf sqd(k * sizeof(double), s_);
+    TATRG_CUDA(cudaMemcpyAsync(sqd.d(), sq.data(), k * sizeof(double), cudaMemcpyHostToDevice, s_));
+    scale_axis(Vt.p(), sqd.d(), 1, k, n, 1, s_);
+    TATRG_CUDA(cudaStreamSynchronize(s_));
+  }
+  OrthResult out;
+  out.R.buf = dalloc(int64_t(k) * n, s_);
+  out.R.rows = k;
+  out.R.cols = n;
+  mm(k, n, k, q.R.p(), k, false, Vt.p(), n, false, out.R.p(), n);
+  out.Q = std::move(q.Q);
+  out.k = k;
+  return out;
+}
+
+SvdResult Engine::svd(const double* A, int64_t m, int64_t n) {
+  SvdResult r;
+  const int64_t k = std::min(m, n);
+  r.S = DevBuf(k * sizeof(double), s_);
+  if (m >= n) {
+    r.U.buf = dalloc(m * n, s_);
+    r.U.rows = m;
+    r.U.cols = n;
+    r.V.buf = dalloc(n * n, s_);
+    r.V.rows = n;
+    r.V.cols = n;
+    jacobi_svd(A, m, int(n), r.U.p(), r.S.d(), r.V.p(), flag(1), s_, &st_);
+  } else {
+    DevBuf At(m * n * sizeof(double), s_);
+    transpose(A, m, n, At.d(), s_);
+    r.V.buf = dalloc(n * m, s_);
+    r.V.rows = n;
+    r.V.cols = m;
+    r.U.buf = dalloc(m * m, s_);
+    r.U.rows = m;
+    r.U.cols = m;
+    jacobi_svd(At.d(), n, int(m), r.V.p(), r.S.d(), r.U.p(), flag(1), s_, &st_);
+  }
+  r.r = int(k);
+  r.s = to_host(r.S.d(), k);
+  TATRG_CHECK(read_flag(1) == 0, TATRG_ENUMERIC, "Jacobi SVD did not converge");
+  for (double x : r.s) TATRG_CHECK(std::isfinite(x), TATRG_ENUMERIC, "non-finite singular value");
+  return r;
+}
+
+SvdResult Engine::rsvd(const Op& apply, const Op& rapply, int64_t rows, int64_t cols,
+                       int64_t ell, int q, const double* omega) {
+  DMat Y;
+  Y.buf = dalloc(rows * ell, s_);
+  apply(omega, ell, Y.p());
+  OrthResult Q = orth(Y.p(), rows, ell);
+  for (int it = 0; it < q; ++it) {
+    DMat Z;
+    Z.buf = dalloc(cols * Q.k, s_);
+    rapply(Q.Q.p(), Q.k, Z.p());
+    OrthResult Qt = orth(Z.p(), cols, Q.k);
+    DMat Y2;
+    Y2.buf = dalloc(rows * Qt.k, s_);
+    apply(Qt.Q.p(), Qt.k, Y2.p());
+    Q = orth(Y2.p(), rows, Qt.k);
+  }
+  DMat Bt;
+  Bt.buf = dalloc(cols * Q.k, s_);
+  rapply(Q.Q.p(), Q.k, Bt.p());          // (Q^T M)^T
+  OrthResult P = orth(Bt.p(), cols, Q.k); // Bt = P R, R: kp x kq
+  const int64_t kq = Q.k, kp = P.k;
+  DevBuf Rt(kq * kp * sizeof(double), s_);
+  transpose(P.R.p(), kp, kq, Rt.d(), s_);  // R^T: kq x kp
+  SvdResult c = svd(Rt.d(), kq, kp);       // R^T = W S Z^T
+  const int64_t r = c.r;
+  SvdResult out;
+  out.r = int(r);
+  out.s = c.s;
+  out.S = std::move(c.S);
+  out.U.buf = dalloc(rows * r, s_);
+  out.U.rows = rows;
+  out.U.cols = r;
+  mm(rows, r, kq, Q.Q.p(), kq, false, c.U.p(), c.U.cols, false, out.U.p(), r);
+  out.V.buf = dalloc(cols * r, s_);
+  out.V.rows = cols;
+  out.V.cols = r;
+  mm(cols, r, kp, P.Q.p(), kp, false, c.V.p(), c.V.cols, false, out.V.p(), r);
+  return out;
+}
+
+SvdResult Engine::rsvd_psd(const double* rho, int64_t n, int64_t ell, int q, const double* omega) {
+  auto app = [&](const double* X, int64_t w, double* Yo) {
+    mm(n, w, n, rho, n, false, X, w, false, Yo, w);
+  };
+  DMat Y;
+  Y.buf = dalloc(n * ell, s_);
+  app(omega, ell, Y.p());
+  OrthResult Q = orth(Y.p(), n, ell);
+  for (int it = 0; it < q; ++it) {
+    DMat Z;
+    Z.buf = dalloc(n * Q.k, s_);
+    app(Q.Q.p(), Q.k, Z.p());
+    OrthResult Qt = orth(Z.p(), n, Q.k);
+    DMat Y2;
+    Y2.buf = dalloc(n * Qt.k, s_);
+    app(Qt.Q.p(), Qt.k, Y2.p());
+    Q = orth(Y2.p(), n, Qt.k);
+  }
+  const int64_t k = Q.k;
+  DMat RQ;
+  RQ.buf = dalloc(n * k, s_);
+  app(Q.Q.p(), k, RQ.p());
+  DevBuf Bm(k * k * sizeof(double), s_);
+  mm(k, k, n, Q.Q.p(), k, true, RQ.p(), k, false, Bm.d(), k);  // Q^T rho Q
+  SvdResult e = svd(Bm.d(), k, k);
+  SvdResult out;
+  out.r = e.r;
+  out.s = e.s;
+  out.S = std::move(e.S);
+  out.U.buf = dalloc(n * e.r, s_);
+  out.U.rows = n;
+  out.U.cols = e.r;
+  mm(n, e.r, k, Q.Q.p(), k, false, e.V.p(), e.V.cols, false, out.U.p(), e.r);
+  return out;
+}
+
+}  // namespace tatrg

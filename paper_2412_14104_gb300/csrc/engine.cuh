@@ -1,0 +1,75 @@
+// Host-side building blocks of the RG step: contraction dispatch, orthonormalisation,
+// small SVDs and the randomized SVDs (Halko, Martinsson & Tropp 2011, Alg. 4.4 + 5.1).
+#pragma once
+
+#include <functional>
+
+#include "kernels.cuh"
+
+namespace tatrg {
+
+// A device matrix, row-major rows x cols.
+struct DMat {
+  DevBuf buf;
+  int64_t rows = 0, cols = 0;
+  double* p() const { return buf.d(); }
+};
+
+struct OrthResult {
+  DMat Q;  // m x k
+  DMat R;  // k x n (upper triangular when k == n)
+  int k = 0;
+};
+
+struct SvdResult {
+  DMat U;  // m x r
+  DMat V;  // n x r
+  DevBuf S;
+  std::vector<double> s;  // host copy, descending
+  int r = 0;
+};
+
+class Engine {
+ public:
+  explicit Engine(cudaStream_t s) : s_(s), flag_(sizeof(int) * 4, s) {}
+  cudaStream_t stream() const { return s_; }
+  Stats& stats() { return st_; }
+
+  // precision of the large contractions (0 = FP64, 1 = 3xTF32, 2 = BF16x3)
+  int prec = 0;
+  bool allow_tc = true;
+
+  void gemm(const GemmDesc& d, const double* A, const double* B, double* C);
+  // row-major C (M x N) = alpha op(A) op(B) + beta C, op = transpose when flag set;
+  // lda etc. are the row lengths of the stored matrices.
+  void mm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta,
+          const double* B, int64_t ldb, bool tb, double* C, int64_t ldc, double alpha = 1.0,
+          double beta = 0.0);
+
+  OrthResult orth(const double* Y, int64_t m, int64_t n);
+  SvdResult svd(const double* A, int64_t m, int64_t n);
+
+  // Randomized SVD of an implicit rows x cols operator: apply(X, w, Y) computes
+  // Y = M X for X (cols x w), rapply(X, w, Z) computes Z = M^T X for X (rows x w).
+  using Op = std::function<void(const double*, int64_t, double*)>;
+  SvdResult rsvd(const Op& apply, const Op& rapply, int64_t rows, int64_t cols, int64_t ell,
+                 int q, const double* omega);
+  // Subspace iteration on a PSD rho (n x n, row-major): returns leading Ritz values in
+  // S and vectors in U (n x k).
+  SvdResult rsvd_psd(const double* rho, int64_t n, int64_t ell, int q, const double* omega);
+
+  std::vector<double> to_host(const double* p, int64_t n);
+  int read_flag(int idx = 0);
+  int* flag(int idx = 0) { return flag_.as<int>() + idx; }
+  double* scratch_double() { return reinterpret_cast<double*>(flag_.as<int>() + 2); }
+
+ private:
+  OrthResult cholqr2(const double* Y, int64_t m, int64_t n, double shift, bool& ok);
+  cudaStream_t s_;
+  Stats st_;
+  DevBuf flag_;
+};
+
+int keep_count(const std::vector<double>& v, double rel, int64_t cap);
+
+}  // namespace tatrg

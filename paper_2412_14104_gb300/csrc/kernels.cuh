@@ -1,0 +1,58 @@
+// Launch wrappers of the library's kernels (host-callable), grouped by file.
+#pragma once
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace tatrg {
+
+// Per-context counters of what was launched.
+struct Stats {
+  long launches = 0;
+  long tc_launches = 0;
+  double flops_f64 = 0.0;
+  double flops_tc = 0.0;  // algorithmic flops routed to the tensor cores
+};
+
+// kernels_f64.cu ----------------------------------------------------------------------
+void gemm_f64(const GemmDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
+              Stats* st);
+void gaussian(uint64_t seed, uint32_t sid, uint32_t replica, int64_t n, double* out,
+              cudaStream_t s);
+// x viewed as [outer, n, inner] is multiplied along n by v^power (power 1, 2, -1, -2=rsqrt)
+void scale_axis(double* x, const double* v, int64_t outer, int64_t n, int64_t inner, int power,
+                cudaStream_t s);
+// dst[off1(e)] = alpha * src[off0(e)] for e over the modes (s0: source, s1: destination)
+void copy_modes(double* dst, const double* src, const ModeIdx& m, double alpha, cudaStream_t s);
+void weighted_colsum(const double* X, int64_t F, int n, double* v, cudaStream_t s);
+void flip_by_sign(double* X, int64_t F, int n, double* Y, int64_t G, const double* v,
+                  cudaStream_t s);
+void trace_asb(const double* A, const double* sv, const double* B, int64_t F, int Da,
+               double* out, cudaStream_t s);
+void sum_all(const double* x, int64_t n, double* out, cudaStream_t s);
+void ising_tensor(double beta, double h, int d, double* T, cudaStream_t s);
+void fill(double* x, int64_t n, double v, cudaStream_t s);
+void check_finite(const double* x, int64_t n, int* bad_dev, cudaStream_t s);
+
+// linalg.cu ---------------------------------------------------------------------------
+// Cholesky G = R^T R of an n x n SPD matrix (row-major); R upper (row-major, zero below).
+// *status_dev = 0 on success, 1 when a pivot is not positive relative to its diagonal.
+void cholesky(const double* G, int n, double* R, int* status_dev, double shift_rel,
+              cudaStream_t s);
+// inverse of an upper-triangular n x n matrix (row-major)
+void tri_inverse(const double* R, int n, double* Rinv, cudaStream_t s);
+// One-sided Jacobi SVD of a row-major m x n (m >= n): U (m x n), S (n), V (n x n) with
+// S descending.  *status_dev = 0 converged, 1 not converged.
+void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double* V,
+                int* status_dev, cudaStream_t s, Stats* st);
+// C (n x n) = A (n x n) * B (n x n), all row-major, small FP64 helper
+void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStream_t s);
+
+// tc_gemm.cu --------------------------------------------------------------------------
+// Split-precision tcgen05 GEMM on multi-mode operands: prec 1 = 3xTF32, 2 = BF16x3.
+bool tc_available();
+void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int prec,
+             cudaStream_t s, Stats* st);
+
+}  // namespace tatrg

@@ -1,0 +1,249 @@
+// Small dense FP64 linear algebra, one thread block per problem: Cholesky (the core of
+// CholeskyQR2), inverse of the triangular factor, and the one-sided (Hestenes) Jacobi SVD
+// used for every core SVD / PSD eigenproblem of the RG step (swap core, triad Gram
+// eigenvectors, squeezer factors and core, re-split).
+#include "kernels.cuh"
+
+namespace tatrg {
+namespace {
+
+// Right-looking Cholesky on a global n x n workspace W (row-major, upper triangle used).
+__global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, double* W,
+                                                        int* status, double shift_rel) {
+  __shared__ int fail;
+  __shared__ double shift;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    fail = 0;
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += G[int64_t(i) * n + i];
+    shift = shift_rel * tr;
+  }
+  __syncthreads();
+  for (int64_t e = tid; e < int64_t(n) * n; e += nt) {
+    int i = int(e / n), k = int(e % n);
+    W[e] = (k >= i) ? G[e] + (i == k ? shift : 0.0) : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      double d = W[int64_t(j) * n + j];
+      double ref = G[int64_t(j) * n + j] + shift;
+      if (!(d > 1e-14 * ref) || !(ref > 0.0)) fail = 1;
+      else W[int64_t(j) * n + j] = sqrt(d);
+    }
+    __syncthreads();
+    if (fail) break;
+    const double djj = W[int64_t(j) * n + j];
+    for (int k = j + 1 + tid; k < n; k += nt) W[int64_t(j) * n + k] /= djj;
+    __syncthreads();
+    const int rem = n - j - 1;
+    const int64_t cnt = int64_t(rem) * rem;
+    for (int64_t e = tid; e < cnt; e += nt) {
+      int i = j + 1 + int(e / rem), k = j + 1 + int(e % rem);
+      if (k >= i) W[int64_t(i) * n + k] -= W[int64_t(j) * n + i] * W[int64_t(j) * n + k];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *status = fail;
+}
+
+// Inverse of an upper-triangular matrix, row by row from the bottom; warp w handles the
+// columns c = w (mod warps) of row i, its lanes split the inner sum.
+__global__ void __launch_bounds__(1024) tri_inverse_kernel(const double* R, int n, double* X) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int64_t e = tid; e < int64_t(n) * n; e += blockDim.x) X[e] = 0.0;
+  __syncthreads();
+  for (int i = n - 1; i >= 0; --i) {
+    const double rii = R[int64_t(i) * n + i];
+    for (int c = i + warp; c < n; c += nw) {
+      double acc = 0.0;
+      for (int k = i + 1 + lane; k <= c; k += 32) acc += R[int64_t(i) * n + k] * X[int64_t(k) * n + c];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) X[int64_t(i) * n + c] = ((c == i ? 1.0 : 0.0) - acc) / rii;
+    }
+    __syncthreads();
+  }
+}
+
+// One-sided Jacobi SVD.  Ac: column-major m x N workspace (N = n rounded up to even, the
+// padding column is zero), Vc: column-major N x N initialised to the identity.
+__global__ void __launch_bounds__(1024) jacobi_kernel(double* Ac, int64_t m, int N, double* Vc,
+                                                      int max_sweeps, double tol, int* status) {
+  __shared__ int rotated;
+  __shared__ double fro2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // Columns whose squared norm is below (4 eps)^2 ||A||_F^2 sit at the rounding floor:
+  // they are treated as converged, otherwise rounding in a large-small pair keeps the
+  // relative inner product above tol forever.
+  if (threadIdx.x == 0) fro2 = 0.0;
+  __syncthreads();
+  {
+    double acc = 0.0;
+    for (int64_t e = threadIdx.x; e < m * N; e += blockDim.x) acc = fma(Ac[e], Ac[e], acc);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) atomicAdd(&fro2, acc);
+  }
+  __syncthreads();
+  const double floor2 = 7.9e-31 * fro2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      for (int k = warp; k < N / 2; k += nw) {
+        int p, q;
+        if (k == 0) { p = N - 1; q = r % (N - 1); }
+        else { p = (r + k) % (N - 1); q = (r + N - 1 - k) % (N - 1); }
+        double* ap = Ac + int64_t(p) * m;
+        double* aq = Ac + int64_t(q) * m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int64_t i = lane; i < m; i += 32) {
+          double x = ap[i], y = aq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+          double zeta = (be - al) / (2.0 * ga);
+          double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          for (int64_t i = lane; i < m; i += 32) {
+            double x = ap[i], y = aq[i];
+            ap[i] = c * x - s * y;
+            aq[i] = s * x + c * y;
+          }
+          double* vp = Vc + int64_t(p) * N;
+          double* vq = Vc + int64_t(q) * N;
+          for (int i = lane; i < N; i += 32) {
+            double x = vp[i], y = vq[i];
+            vp[i] = c * x - s * y;
+            vq[i] = s * x + c * y;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (!rotated) break;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *status = (sweep >= max_sweeps) ? 1 : 0;
+}
+
+// Column norms, descending ranks (ties by index) and the scattered outputs.
+__global__ void __launch_bounds__(1024) jacobi_finish_kernel(const double* Ac, int64_t m, int n,
+                                                             int N, const double* Vc, double* U,
+                                                             double* S, double* V) {
+  extern __shared__ double sig[];
+  int* rank = reinterpret_cast<int*>(sig + N);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = warp; j < n; j += nw) {
+    double acc = 0.0;
+    for (int64_t i = lane; i < m; i += 32) { double x = Ac[int64_t(j) * m + i]; acc = fma(x, x, acc); }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sig[j] = sqrt(acc);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int rk = 0;
+    for (int i = 0; i < n; ++i) rk += (sig[i] > sig[j]) || (sig[i] == sig[j] && i < j);
+    rank[j] = rk;
+    S[rk] = sig[j];
+  }
+  __syncthreads();
+  for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) {
+    int64_t i = e / n;
+    int j = int(e - i * n);
+    double sj = sig[j];
+    U[i * n + rank[j]] = sj > 0.0 ? Ac[int64_t(j) * m + i] / sj : 0.0;
+  }
+  for (int64_t e = threadIdx.x; e < int64_t(n) * n; e += blockDim.x) {
+    int i = int(e / n), j = int(e % n);
+    V[int64_t(i) * n + rank[j]] = Vc[int64_t(j) * N + i];
+  }
+}
+
+__global__ void to_colmajor_kernel(const double* A, int64_t m, int n, int N, double* Ac, double* Vc) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < m * N + int64_t(N) * N;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    if (e < m * N) {
+      int64_t j = e / m, i = e - (e / m) * m;
+      Ac[e] = (j < n) ? A[i * n + j] : 0.0;
+    } else {
+      int64_t f = e - m * N;
+      int64_t j = f / N, i = f - (f / N) * N;
+      Vc[f] = (i == j) ? 1.0 : 0.0;
+    }
+  }
+}
+
+__global__ void transpose_kernel(const double* A, int64_t rows, int64_t cols, double* At) {
+  __shared__ double tile[32][33];
+  int64_t bx = int64_t(blockIdx.x) * 32, by = int64_t(blockIdx.y) * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int64_t r = by + k, c = bx + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = A[r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int64_t c = bx + k, r = by + threadIdx.x;
+    if (r < rows && c < cols) At[c * rows + r] = tile[threadIdx.x][k];
+  }
+}
+}  // namespace
+
+void cholesky(const double* G, int n, double* R, int* status_dev, double shift_rel,
+              cudaStream_t s) {
+  check_extent(G, int64_t(n) * n - 1, sizeof(double), "cholesky input");
+  check_extent(R, int64_t(n) * n - 1, sizeof(double), "cholesky output");
+  cholesky_kernel<<<1, 1024, 0, s>>>(G, n, R, status_dev, shift_rel);
+  TATRG_CUDA(cudaGetLastError());
+}
+
+void tri_inverse(const double* R, int n, double* Rinv, cudaStream_t s) {
+  check_extent(R, int64_t(n) * n - 1, sizeof(double), "tri_inverse input");
+  check_extent(Rinv, int64_t(n) * n - 1, sizeof(double), "tri_inverse output");
+  tri_inverse_kernel<<<1, 1024, 0, s>>>(R, n, Rinv);
+  TATRG_CUDA(cudaGetLastError());
+}
+
+void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double* V,
+                int* status_dev, cudaStream_t s, Stats* st) {
+  TATRG_CHECK(m >= n && n >= 1 && n <= 1024, TATRG_EINVAL, "jacobi_svd: need m >= n, 1 <= n <= 1024");
+  check_extent(A, m * n - 1, sizeof(double), "jacobi input");
+  check_extent(U, m * n - 1, sizeof(double), "jacobi U");
+  check_extent(S, n - 1, sizeof(double), "jacobi S");
+  check_extent(V, int64_t(n) * n - 1, sizeof(double), "jacobi V");
+  const int N = n + (n & 1);
+  DevBuf ac(size_t(m) * N * sizeof(double), s), vc(size_t(N) * N * sizeof(double), s);
+  int64_t tot = m * N + int64_t(N) * N;
+  to_colmajor_kernel<<<int(std::min<int64_t>(cdiv(tot, 256), 2048)), 256, 0, s>>>(A, m, n, N,
+                                                                                  ac.d(), vc.d());
+  TATRG_CUDA(cudaGetLastError());
+  const double tol = std::max(1e-15, 2.220446049250313e-16 * std::sqrt(double(m)));
+  int threads = 32 * std::max(1, std::min(32, N / 2));
+  jacobi_kernel<<<1, threads, 0, s>>>(ac.d(), m, N, vc.d(), 60, tol, status_dev);
+  TATRG_CUDA(cudaGetLastError());
+  size_t sm = N * sizeof(double) + N * sizeof(int);
+  jacobi_finish_kernel<<<1, 1024, sm, s>>>(ac.d(), m, n, N, vc.d(), U, S, V);
+  TATRG_CUDA(cudaGetLastError());
+  if (st) st->launches += 3;
+}
+
+void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStream_t s) {
+  if (rows == 0 || cols == 0) return;
+  check_extent(A, rows * cols - 1, sizeof(double), "transpose input");
+  check_extent(At, rows * cols - 1, sizeof(double), "transpose output");
+  dim3 grid(unsigned(cdiv(cols, 32)), unsigned(cdiv(rows, 32)));
+  transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(A, rows, cols, At);
+  TATRG_CUDA(cudaGetLastError());
+}
+
+}  // namespace tatrg

@@ -1,0 +1,101 @@
+"""GPU parity of the library's building blocks (through the C ABI) against the oracle and
+plain NumPy: Philox sketch, multi-mode contraction, Jacobi SVD, orthonormalisation."""
+import numpy as np
+import pytest
+
+import paper_2412_14104_gb300 as tg
+from oracle import philox, rla
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need CUDA"
+    return t
+
+
+def _dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("rows,cols,replica", [(1, 1, 0), (7, 13, 0), (300, 61, 3)])
+def test_philox_sketch_matches_oracle(torch, rows, cols, replica):
+    """P12: same counters, keys and Box-Muller; the integer stream is identical, the
+    Gaussians agree to the last few ulp of the two libms."""
+    sid = philox.stream_id(5, 2)
+    out = torch.empty(rows * cols, dtype=torch.float64, device="cuda")
+    tg.gaussian(2 ** 40 + 17, sid, rows, cols, out, replica=replica)
+    torch.cuda.synchronize()
+    want = philox.gaussian(2 ** 40 + 17, sid, rows, cols, replica).ravel()
+    got = out.cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-14)
+
+
+def _contract_case(rng, torch, prec, tol):
+    # C[i,j,a,b] (stored [a,i,b,j]) = sum_{k,l} A[k,i,l,a] B[b,l,j,k]
+    I, J, a, b, K, L = 5, 7, 3, 4, 6, 9
+    A = rng.standard_normal((K, I, L, a))
+    B = rng.standard_normal((b, L, J, K))
+    C0 = rng.standard_normal((a, I, b, J))
+    want = 0.5 * np.einsum("kila,bljk->aibj", A, B) + 2.0 * C0
+    dA, dB, dC = _dev(torch, A), _dev(torch, B), _dev(torch, C0)
+    # m = (i, a): A strides (L*a, 1), C strides (b*J, I*b*J); n = (j, b)
+    m = [(I, L * a, b * J), (a, 1, I * b * J)]
+    n = [(J, K, 1), (b, L * J * K, J)]
+    k = [(K, I * L * a, 1), (L, a, J * K)]
+    tg.contract(m, n, k, dA, dB, dC, alpha=0.5, beta=2.0, precision=prec)
+    torch.cuda.synchronize()
+    got = dC.cpu().numpy()
+    assert np.max(np.abs(got - want)) < tol * np.max(np.abs(want))
+
+
+def test_contract_fp64_multimode(torch):
+    rng = np.random.default_rng(0)
+    _contract_case(rng, torch, tg.FP64, 1e-14)
+
+
+def test_contract_fp64_split_k(torch):
+    """A long K (split across blocks and summed atomically) and a transposed operand."""
+    rng = np.random.default_rng(1)
+    M, N, K = 37, 45, 20000
+    A = rng.standard_normal((K, M))
+    B = rng.standard_normal((K, N))
+    C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    tg.contract([(M, 1, N)], [(N, 1, 1)], [(K, M, N)], _dev(torch, A), _dev(torch, B), C)
+    torch.cuda.synchronize()
+    assert np.allclose(C.cpu().numpy(), A.T @ B, rtol=1e-12, atol=1e-10)
+
+
+@pytest.mark.parametrize("m,n", [(9, 9), (40, 17), (200, 144), (1, 1)])
+def test_jacobi_svd(torch, m, n):
+    rng = np.random.default_rng(m + n)
+    A = rng.standard_normal((m, n)) * (0.7 ** np.arange(n))[None, :]
+    U = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    S = torch.empty(n, dtype=torch.float64, device="cuda")
+    V = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    tg.svd(_dev(torch, A), U, S, V)
+    u, s, v = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    s_ref = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(s, s_ref, rtol=1e-12, atol=1e-14 * s_ref[0])
+    assert np.allclose((u * s) @ v.T, A, atol=1e-13 * s_ref[0])
+    assert np.allclose(v.T @ v, np.eye(n), atol=1e-13)
+
+
+def test_orth_full_rank_and_rank_deficient(torch):
+    rng = np.random.default_rng(3)
+    m, n = 500, 24
+    for rank in (24, 10):
+        Y = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n))
+        Q = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        R = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        k = tg.orth(_dev(torch, Y), Q, R)
+        q = Q.cpu().numpy().ravel()[: m * k].reshape(m, k)
+        r = R.cpu().numpy().ravel()[: k * n].reshape(k, n)
+        assert k == rank
+        assert np.allclose(q.T @ q, np.eye(k), atol=1e-13)
+        assert np.allclose(q @ r, Y, atol=1e-12 * np.abs(Y).max())
+        if k == n:  # unique thin QR with non-negative diagonal
+            q_ref, r_ref = rla.orth(Y)
+            assert np.allclose(q, q_ref, atol=1e-11)
