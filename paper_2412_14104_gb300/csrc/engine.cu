@@ -100,53 +100,23 @@ OrthResult Engine::orth(const double* Y, int64_t m, int64_t n) {
     r = cholqr2(Y, m, n, prec == 0 ? 0.0 : 1e-6, ok);
     if (ok) return r;
   }
-  // Rank-revealing fallback: eigen-decomposition of the Gram, drop directions whose
-  // eigenvalue is below the relative cut, whiten, then CholeskyQR2 on the whitened basis.
-  DevBuf G(n * n * sizeof(double), s_);
-  mm(n, n, m, Y, n, true, Y, n, false, G.d(), n);
-  SvdResult e = svd(G.d(), n, n);
-  const double cut = prec == 0 ? 1e-14 : 1e-6;
-  int k = keep_count(e.s, cut, std::min<int64_t>(m, n));
+  // Rank-revealing fallback: one-sided Jacobi SVD of Y itself (no squared condition
+  // number), Y = U S V^T; keep the directions above the rounding floor: Q = U_k,
+  // R = S_k V_k^T.
+  SvdResult e = svd(Y, m, n);
+  const double cut = prec == 0 ? 1e-14 : 1e-7;
+  int k = keep_count(e.s, cut, std::min(m, n));
   TATRG_CHECK(k >= 1, TATRG_ENUMERIC, "orth: zero matrix");
-  // W = V_k diag(lambda^-1/2)  (n x k)
-  DMat W;
-  W.buf = dalloc(n * k, s_);
-  W.rows = n;
-  W.cols = k;
-  {
-    ModeIdx cp = modes({{n, e.r, k}, {k, 1, 1}});
-    copy_modes(W.p(), e.V.p(), cp, 1.0, s_);
-    scale_axis(W.p(), e.S.d(), n, k, 1, -2, s_);
-  }
-  DMat Y1;
-  Y1.buf = dalloc(m * k, s_);
-  Y1.rows = m;
-  Y1.cols = k;
-  mm(m, k, n, Y, n, false, W.p(), k, false, Y1.p(), k);
-  int saved = prec;
-  prec = 0;  // the whitened basis is refined in FP64
-  OrthResult q = cholqr2(Y1.p(), m, k, 0.0, ok);
-  prec = saved;
-  TATRG_CHECK(ok, TATRG_ENUMERIC, "orth: CholeskyQR2 failed on the whitened basis");
-  // R = Rq diag(lambda^1/2) V_k^T  (k x n)
-  DMat Vt;
-  Vt.buf = dalloc(int64_t(k) * n, s_);
-  {
-    ModeIdx cp = modes({{k, 1, n}, {n, e.r, 1}});  // Vt[j, i] = V[i, j]
-    copy_modes(Vt.p(), e.V.p(), cp, 1.0, s_);
-    std::vector<double> sq(e.s.begin(), e.s.begin() + k);
-    for (auto& x : sq) x = std::sqrt(x);
-    DevBuf sqd(k * sizeof(double), s_);
-    TATRG_CUDA(cudaMemcpyAsync(sqd.d(), sq.data(), k * sizeof(double), cudaMemcpyHostToDevice, s_));
-    scale_axis(Vt.p(), sqd.d(), 1, k, n, 1, s_);
-    TATRG_CUDA(cudaStreamSynchronize(s_));
-  }
   OrthResult out;
+  out.Q.buf = dalloc(m * k, s_);
+  out.Q.rows = m;
+  out.Q.cols = k;
+  copy_modes(out.Q.p(), e.U.p(), modes({{m, e.U.cols, k}, {k, 1, 1}}), 1.0, s_);
   out.R.buf = dalloc(int64_t(k) * n, s_);
   out.R.rows = k;
   out.R.cols = n;
-  mm(k, n, k, q.R.p(), k, false, Vt.p(), n, false, out.R.p(), n);
-  out.Q = std::move(q.Q);
+  copy_modes(out.R.p(), e.V.p(), modes({{k, 1, n}, {n, e.V.cols, 1}}), 1.0, s_);  // V_k^T
+  scale_axis(out.R.p(), e.S.d(), 1, k, n, 1, s_);
   out.k = k;
   return out;
 }

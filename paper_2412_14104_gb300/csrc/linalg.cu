@@ -137,36 +137,47 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* Ac, int64_t m, int
   if (threadIdx.x == 0) *status = (sweep >= max_sweeps) ? 1 : 0;
 }
 
-// Column norms, descending ranks (ties by index) and the scattered outputs.
-__global__ void __launch_bounds__(1024) jacobi_finish_kernel(const double* Ac, int64_t m, int n,
-                                                             int N, const double* Vc, double* U,
-                                                             double* S, double* V) {
-  extern __shared__ double sig[];
-  int* rank = reinterpret_cast<int*>(sig + N);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < n; j += nw) {
-    double acc = 0.0;
-    for (int64_t i = lane; i < m; i += 32) { double x = Ac[int64_t(j) * m + i]; acc = fma(x, x, acc); }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) sig[j] = sqrt(acc);
-  }
+// Column norms (one block per column), descending ranks (ties by index) and the
+// scattered outputs U[:, rank_j] = a_j / |a_j|, S[rank_j] = |a_j|, V[:, rank_j] = v_j.
+__global__ void col_norms_kernel(const double* Ac, int64_t m, double* sig) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) { double x = Ac[int64_t(j) * m + i]; acc = fma(x, x, acc); }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+    sig[j] = sqrt(t);
+  }
+}
+
+__global__ void rank_kernel(const double* sig, int n, int* rank, double* S) {
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     int rk = 0;
     for (int i = 0; i < n; ++i) rk += (sig[i] > sig[j]) || (sig[i] == sig[j] && i < j);
     rank[j] = rk;
     S[rk] = sig[j];
   }
-  __syncthreads();
-  for (int64_t e = threadIdx.x; e < m * n; e += blockDim.x) {
-    int64_t i = e / n;
-    int j = int(e - i * n);
-    double sj = sig[j];
-    U[i * n + rank[j]] = sj > 0.0 ? Ac[int64_t(j) * m + i] / sj : 0.0;
-  }
-  for (int64_t e = threadIdx.x; e < int64_t(n) * n; e += blockDim.x) {
-    int i = int(e / n), j = int(e % n);
-    V[int64_t(i) * n + rank[j]] = Vc[int64_t(j) * N + i];
+}
+
+__global__ void svd_scatter_kernel(const double* Ac, int64_t m, int n, int N, const double* Vc,
+                                   const double* sig, const int* rank, double* U, double* V) {
+  const int64_t tu = m * n, tv = int64_t(n) * n;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < tu + tv;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    if (e < tu) {
+      int64_t i = e / n;
+      int j = int(e - i * n);
+      double sj = sig[j];
+      U[i * n + rank[j]] = sj > 0.0 ? Ac[int64_t(j) * m + i] / sj : 0.0;
+    } else {
+      int64_t f = e - tu;
+      int i = int(f / n), j = int(f % n);
+      V[int64_t(i) * n + rank[j]] = Vc[int64_t(j) * N + i];
+    }
   }
 }
 
@@ -196,6 +207,75 @@ __global__ void transpose_kernel(const double* A, int64_t rows, int64_t cols, do
     int64_t c = bx + k, r = by + threadIdx.x;
     if (r < rows && c < cols) At[c * rows + r] = tile[threadIdx.x][k];
   }
+}
+
+// Multi-block one-sided Jacobi for tall matrices: one launch per round of the
+// round-robin schedule, one block per column pair, the block's threads split the rows.
+__global__ void __launch_bounds__(256) tall_jacobi_round_kernel(double* Ac, int64_t m, int N,
+                                                                double* Vc, int r, double tol,
+                                                                const double* fro2, int* rotated) {
+  __shared__ double red[3][8];
+  __shared__ double cs[2];
+  __shared__ int doit;
+  const int k = blockIdx.x;
+  int p, q;
+  if (k == 0) { p = N - 1; q = r % (N - 1); }
+  else { p = (r + k) % (N - 1); q = (r + N - 1 - k) % (N - 1); }
+  double* ap = Ac + int64_t(p) * m;
+  double* aq = Ac + int64_t(q) * m;
+  double al = 0.0, be = 0.0, ga = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    double x = ap[i], y = aq[i];
+    al = fma(x, x, al);
+    be = fma(y, y, be);
+    ga = fma(x, y, ga);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { red[0][warp] = al; red[1][warp] = be; red[2][warp] = ga; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    al = be = ga = 0.0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) { al += red[0][w]; be += red[1][w]; ga += red[2][w]; }
+    const double floor2 = 7.9e-31 * (*fro2);
+    doit = (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) ? 1 : 0;
+    if (doit) {
+      double zeta = (be - al) / (2.0 * ga);
+      double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      double c = 1.0 / sqrt(1.0 + t * t);
+      cs[0] = c;
+      cs[1] = c * t;
+      *rotated = 1;
+    }
+  }
+  __syncthreads();
+  if (!doit) return;
+  const double c = cs[0], sn = cs[1];
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+    double x = ap[i], y = aq[i];
+    ap[i] = c * x - sn * y;
+    aq[i] = sn * x + c * y;
+  }
+  double* vp = Vc + int64_t(p) * N;
+  double* vq = Vc + int64_t(q) * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double x = vp[i], y = vq[i];
+    vp[i] = c * x - sn * y;
+    vq[i] = sn * x + c * y;
+  }
+}
+
+__global__ void sumsq_kernel(const double* x, int64_t n, double* out) {
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n;
+       e += int64_t(gridDim.x) * blockDim.x)
+    acc = fma(x[e], x[e], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 }  // namespace
 
@@ -228,13 +308,44 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
                                                                                   ac.d(), vc.d());
   TATRG_CUDA(cudaGetLastError());
   const double tol = std::max(1e-15, 2.220446049250313e-16 * std::sqrt(double(m)));
-  int threads = 32 * std::max(1, std::min(32, N / 2));
-  jacobi_kernel<<<1, threads, 0, s>>>(ac.d(), m, N, vc.d(), 60, tol, status_dev);
+  if (m * N <= (int64_t(1) << 17) || N < 4) {
+    int threads = 32 * std::max(1, std::min(32, N / 2));
+    jacobi_kernel<<<1, threads, 0, s>>>(ac.d(), m, N, vc.d(), 60, tol, status_dev);
+    TATRG_CUDA(cudaGetLastError());
+  } else {
+    // tall: one block per pair and one launch per round; the host reads the rotation flag
+    // once per sweep.
+    DevBuf aux(2 * sizeof(double), s);
+    double* fro2 = aux.d();
+    int* rot = reinterpret_cast<int*>(aux.d() + 1);
+    TATRG_CUDA(cudaMemsetAsync(fro2, 0, sizeof(double), s));
+    sumsq_kernel<<<int(std::min<int64_t>(cdiv(m * N, 256), 1024)), 256, 0, s>>>(ac.d(), m * N, fro2);
+    TATRG_CUDA(cudaGetLastError());
+    int converged = 0, sweep = 0;
+    for (; sweep < 60 && !converged; ++sweep) {
+      TATRG_CUDA(cudaMemsetAsync(rot, 0, sizeof(int), s));
+      for (int r = 0; r < N - 1; ++r) {
+        tall_jacobi_round_kernel<<<N / 2, 256, 0, s>>>(ac.d(), m, N, vc.d(), r, tol, fro2, rot);
+        TATRG_CUDA(cudaGetLastError());
+      }
+      int h = 0;
+      TATRG_CUDA(cudaMemcpyAsync(&h, rot, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TATRG_CUDA(cudaStreamSynchronize(s));
+      converged = (h == 0);
+      if (st) st->launches += N - 1;
+    }
+    int flag = converged ? 0 : 1;
+    TATRG_CUDA(cudaMemcpyAsync(status_dev, &flag, sizeof(int), cudaMemcpyHostToDevice, s));
+    TATRG_CUDA(cudaStreamSynchronize(s));
+  }
+  DevBuf sig(n * sizeof(double), s), rk(n * sizeof(int), s);
+  col_norms_kernel<<<n, 256, 0, s>>>(ac.d(), m, sig.d());
+  rank_kernel<<<1, 1024, 0, s>>>(sig.d(), n, rk.as<int>(), S);
+  int64_t tot2 = m * n + int64_t(n) * n;
+  svd_scatter_kernel<<<int(std::min<int64_t>(cdiv(tot2, 256), 152 * 16)), 256, 0, s>>>(
+      ac.d(), m, n, N, vc.d(), sig.d(), rk.as<int>(), U, V);
   TATRG_CUDA(cudaGetLastError());
-  size_t sm = N * sizeof(double) + N * sizeof(int);
-  jacobi_finish_kernel<<<1, 1024, sm, s>>>(ac.d(), m, n, N, vc.d(), U, S, V);
-  TATRG_CUDA(cudaGetLastError());
-  if (st) st->launches += 3;
+  if (st) st->launches += 5;
 }
 
 void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStream_t s) {

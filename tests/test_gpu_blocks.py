@@ -68,7 +68,7 @@ def test_contract_fp64_split_k(torch):
     assert np.allclose(C.cpu().numpy(), A.T @ B, rtol=1e-12, atol=1e-10)
 
 
-@pytest.mark.parametrize("m,n", [(9, 9), (40, 17), (200, 144), (1, 1)])
+@pytest.mark.parametrize("m,n", [(9, 9), (40, 17), (200, 144), (1, 1), (6000, 40)])
 def test_jacobi_svd(torch, m, n):
     rng = np.random.default_rng(m + n)
     A = rng.standard_normal((m, n)) * (0.7 ** np.arange(n))[None, :]
@@ -99,3 +99,36 @@ def test_orth_full_rank_and_rank_deficient(torch):
         if k == n:  # unique thin QR with non-negative diagonal
             q_ref, r_ref = rla.orth(Y)
             assert np.allclose(q, q_ref, atol=1e-11)
+
+
+def test_orth_keeps_small_but_real_directions():
+    """A rank-deficient Y whose nonzero singular values span 1 .. 1e-9: the orthonormal
+    basis must keep every nonzero direction (a Gram-based method loses those below ~1e-7,
+    where their squares reach the rounding level of the Gram) and span the range of Y to
+    the accuracy the rounding of Y itself allows (~eps / 1e-9)."""
+    rng = np.random.default_rng(7)
+    m, n, rank = 300, 20, 14
+    U, _ = np.linalg.qr(rng.standard_normal((m, rank)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, rank)))
+    S = np.logspace(0, -9, rank)
+    Y = (U * S) @ V.T
+    Q = torch_empty((m, n))
+    R = torch_empty((n, n))
+    k = tg.orth(_dev(_torch(), Y), Q, R)
+    assert k == rank
+    q = Q.cpu().numpy().ravel()[: m * k].reshape(m, k)
+    r = R.cpu().numpy().ravel()[: k * n].reshape(k, n)
+    assert np.allclose(q.T @ q, np.eye(k), atol=1e-13)
+    assert np.allclose(q @ r, Y, atol=1e-14)
+    # same subspace as the exact range of Y
+    assert np.linalg.norm(U - q @ (q.T @ U)) < 1e-5
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def torch_empty(shape):
+    import torch
+    return torch.empty(shape, dtype=torch.float64, device="cuda")
