@@ -61,6 +61,9 @@ typedef struct {
   unsigned long long seed; /* Philox key of all Gaussian sketches */
   int checkpoint_every;    /* steps between checkpoints of the reverse sweep (0: 4) */
   int split_from_step;     /* steps before this one run in FP64 whatever the precision */
+  int split_stages;        /* bit mask of the stages whose large contractions use the split
+                              precision: 1 swap, 2 triad, 4 squeezers, 8 contraction,
+                              16 re-split; 0 means all */
 } tatrg_params;
 
 /* Create a context on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).

@@ -13,6 +13,14 @@
   that w . v > 0, with w_i = (fmix32(i + 1) + 0.5) / 2^32 - 0.5 (the MurmurHash3
   32-bit finaliser).  A fixed, structureless weight avoids the exact magnitude ties that
   the symmetric Ising tensors produce under a "largest entry positive" rule.
+* ``canonical_basis``: lattice symmetries make singular values exactly degenerate; any
+  orthonormal basis of such a multiplet is correct, but a later Gaussian sketch acts on the
+  basis, so it must be fixed.  The columns V_M of a multiplet are rotated to V_M O with O
+  the orthogonal polar factor of V_M^T W, W_j(i) = (fmix32((i + 1) xor (j * 0x9E3779B9))
+  + 0.5) / 2^32 - 0.5.  The result does not depend on the basis the solver returned, and for
+  a single vector it is the sign rule above.
+* ``multiplet_cut``: a truncation never splits a multiplet; the cut moves down to the
+  multiplet's first member.
 """
 import numpy as np
 
@@ -39,6 +47,48 @@ def fix_sign(V):
     w = sign_weights(V.shape[0])
     sgn = np.where(w @ V < 0.0, -1.0, 1.0)
     return V * sgn[None, :], sgn
+
+
+def multiplets(vals, tau):
+    """Index ranges [a, b) of runs whose consecutive gaps are <= tau times the larger value."""
+    out = []
+    a = 0
+    n = len(vals)
+    for i in range(1, n + 1):
+        if i == n or vals[i - 1] - vals[i] > tau * vals[i - 1]:
+            if i - a > 1:
+                out.append((a, i))
+            a = i
+    return out
+
+
+def multiplet_cut(vals, k, tau):
+    """Largest k' <= k that does not cut a multiplet (k itself when nothing is cut)."""
+    if k <= 0 or k >= len(vals):
+        return k
+    for a, b in multiplets(vals, tau):
+        if a < k < b:
+            return a if a > 0 else b
+    return k
+
+
+def basis_weights(n, m):
+    i = np.arange(1, n + 1, dtype=np.uint64)[:, None]
+    j = (np.arange(m, dtype=np.uint64) * np.uint64(0x9E3779B9)) & _MASK
+    return (_fmix32(i ^ j[None, :]).astype(np.float64) + 0.5) * (1.0 / 4294967296.0) - 0.5
+
+
+def canonical_basis(V, vals, tau):
+    """Rotate the columns of V inside each multiplet of vals (and flip single columns) to
+    the canonical basis; returns (V', O) with V' = V O, O block-diagonal orthogonal."""
+    n, k = V.shape
+    O = np.diag(np.where(sign_weights(n) @ V < 0.0, -1.0, 1.0))
+    for a, b in multiplets(vals[:k], tau):
+        W = basis_weights(n, b - a)
+        Gm = V[:, a:b].T @ W
+        U, _, Vt = np.linalg.svd(Gm)
+        O[a:b, a:b] = U @ Vt
+    return V @ O, O
 
 
 def orth(Y):

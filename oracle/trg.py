@@ -25,6 +25,9 @@ Readings where the paper is silent (each repeated in the design notes):
   the full dimension the exact SVD / eigensolver is used instead;
 * cut-offs: singular values / eigenvalues at or below 1e-14 of the largest are dropped;
   squeezer singular values at or below 1e-12 of the largest are dropped;
+* degenerate multiplets (consecutive singular values within a relative gap TAU = 1e-10) are
+  never cut, and the bases that later sketches act on (the bond index of A', B' and the new
+  leg of M, N) are put into the canonical basis of ``rla.canonical_basis``;
 * squeezer construction (Eq. 5 gives only the cost function): rho_L = R_L^T R_L,
   rho_R = R_R^T R_R, C = R_L R_R^T = U S V^T, M = R_R^T V_k S_k^-1/2,
   N = S_k^-1/2 U_k^T R_L, which minimises || R_L (1 - M N) R_R^T ||;
@@ -38,6 +41,7 @@ import numpy as np
 from . import philox, rla
 
 STAGES = ("swap", "triad", "squeeze", "contract", "resplit")
+TAU = 1e-10  # relative gap (s_i - s_i+1) / s_i below which values form one multiplet
 
 
 class Params:
@@ -157,7 +161,7 @@ def bond_swap(A, s, B, p, step, cnt=None, info=None):
                              p.replica)
         U, S, V = rla.rsvd(op, ell, p.q, om)
         exact = False
-    Dg = rla.keep_count(S, 1e-14, p.cap())
+    Dg = rla.multiplet_cut(S, rla.keep_count(S, 1e-14, p.cap()), TAU)
     X, sgn = rla.fix_sign(U[:, :Dg])
     Y = V[:, :Dg] * sgn[None, :]
     if info is not None:
@@ -304,12 +308,12 @@ def squeezers(rho_l, rho_r, p, step, cnt=None, info=None):
         RR = _factor(rho_r[nu - 1], p, step, philox.KIND_SQ_RIGHT + nu - 1, cnt)
         C = RL @ RR.T
         U, S, V = rla.svd_desc(C)
-        k = rla.keep_count(S, 1e-12, p.cap())
+        k = rla.multiplet_cut(S, rla.keep_count(S, 1e-12, p.cap()), TAU)
         isq = 1.0 / np.sqrt(S[:k])
         M = (RR.T @ V[:, :k]) * isq[None, :]
         N = (U[:, :k] * isq[None, :]).T @ RL
-        M, sgn = rla.fix_sign(M)
-        N = N * sgn[:, None]
+        M, O = rla.canonical_basis(M, S[:k], TAU)
+        N = O.T @ N
         Dn = int(round(math.sqrt(M.shape[0])))
         Ms.append(M.reshape(Dn, Dn, k))
         Ns.append(N.reshape(k, Dn, Dn))
@@ -381,8 +385,8 @@ def resplit(phi, psi, p, cnt=None, info=None):
     rot = tuple(range(1, d)) + (0, d)
     An = np.ascontiguousarray(np.transpose(An, rot))
     Bn = np.ascontiguousarray(np.transpose(Bn, rot))
-    am, sgn = rla.fix_sign(An.reshape(-1, Da))
-    bm = Bn.reshape(-1, Da) * sgn[None, :]
+    am, O = rla.canonical_basis(An.reshape(-1, Da), s, TAU)
+    bm = Bn.reshape(-1, Da) @ O
     if info is not None:
         info["s"] = s.copy()
         info["c"] = c

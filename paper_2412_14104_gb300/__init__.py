@@ -29,7 +29,7 @@ class Params(ctypes.Structure):
     _fields_ = [("chi", ctypes.c_int), ("r", ctypes.c_int), ("q", ctypes.c_int),
                 ("method", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("checkpoint_every", ctypes.c_int),
-                ("split_from_step", ctypes.c_int)]
+                ("split_from_step", ctypes.c_int), ("split_stages", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -106,8 +106,8 @@ class Context:
     """One RG run on the current CUDA device (tatrg_ctx)."""
 
     def __init__(self, chi, r, q=2, method=TRIAD, precision=FP64, seed=0, split_from_step=0,
-                 stream=None):
-        self.params = Params(chi, r, q, method, precision, seed, 4, split_from_step)
+                 split_stages=0, stream=None):
+        self.params = Params(chi, r, q, method, precision, seed, 4, split_from_step, split_stages)
         h = ctypes.c_void_p()
         _check(lib().tatrg_create(ctypes.byref(self.params), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h

@@ -28,6 +28,8 @@ void copy_modes(double* dst, const double* src, const ModeIdx& m, double alpha, 
 void weighted_colsum(const double* X, int64_t F, int n, double* v, cudaStream_t s);
 void flip_by_sign(double* X, int64_t F, int n, double* Y, int64_t G, const double* v,
                   cudaStream_t s);
+// G (m x m) = X[:, a:a+m]^T W with the hashed basis weights W (F x m)
+void multiplet_overlap(const double* X, int64_t F, int n, int a, int m, double* G, cudaStream_t s);
 void trace_asb(const double* A, const double* sv, const double* B, int64_t F, int Da,
                double* out, cudaStream_t s);
 void sum_all(const double* x, int64_t n, double* out, cudaStream_t s);
@@ -52,6 +54,8 @@ void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStre
 // tc_gemm.cu --------------------------------------------------------------------------
 // Split-precision tcgen05 GEMM on multi-mode operands: prec 1 = 3xTF32, 2 = BF16x3.
 bool tc_available();
+// reads (and optionally clears) the flag a timed-out tensor-core wait raises
+int tc_error_flag(bool reset);
 void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int prec,
              cudaStream_t s, Stats* st);
 

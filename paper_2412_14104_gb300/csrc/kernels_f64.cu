@@ -343,6 +343,28 @@ __global__ void flip_kernel(double* X, int64_t F, int n, double* Y, int64_t G,
   }
 }
 
+// G[i, j] += sum_f X[f, a + i] w_j(f) for row-major X (F x n), i, j < m (m <= 32), with
+// w_j(f) = (fmix32((f + 1) xor (j * 0x9E3779B9)) + 0.5) / 2^32 - 0.5.
+__global__ void multiplet_overlap_kernel(const double* X, int64_t F, int n, int a, int m,
+                                         double* G) {
+  __shared__ double part[32 * 32];
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) part[i] = 0.0;
+  __syncthreads();
+  for (int64_t f = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; f < F;
+       f += int64_t(gridDim.x) * blockDim.x) {
+    double w[32];
+    for (int j = 0; j < m; ++j)
+      w[j] = (double(fmix32(uint32_t(f + 1) ^ (uint32_t(j) * 0x9E3779B9u))) + 0.5) *
+                 (1.0 / 4294967296.0) - 0.5;
+    for (int i = 0; i < m; ++i) {
+      const double x = X[f * n + a + i];
+      for (int j = 0; j < m; ++j) atomicAdd(&part[i * m + j], x * w[j]);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < m * m; i += blockDim.x) atomicAdd(&G[i], part[i]);
+}
+
 __global__ void sum_kernel(const double* x, int64_t n, double* out) {
   double acc = 0.0;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n;
@@ -448,6 +470,15 @@ void trace_asb(const double* A, const double* sv, const double* B, int64_t F, in
   check_extent(A, F * Da - 1, sizeof(double), "trace A");
   check_extent(B, F * Da - 1, sizeof(double), "trace B");
   trace_kernel<<<grid_for(F * Da), 256, 0, s>>>(A, sv, B, F, Da, out);
+  TATRG_CUDA(cudaGetLastError());
+}
+
+void multiplet_overlap(const double* X, int64_t F, int n, int a, int m, double* G, cudaStream_t s) {
+  TATRG_CHECK(m >= 1 && m <= 32 && a >= 0 && a + m <= n, TATRG_EINVAL, "multiplet_overlap: bad block");
+  check_extent(X, F * n - 1, sizeof(double), "multiplet_overlap");
+  check_extent(G, int64_t(m) * m - 1, sizeof(double), "multiplet_overlap G");
+  fill(G, int64_t(m) * m, 0.0, s);
+  multiplet_overlap_kernel<<<int(std::min<int64_t>(cdiv(F, 256), 608)), 256, 0, s>>>(X, F, n, a, m, G);
   TATRG_CUDA(cudaGetLastError());
 }
 

@@ -19,6 +19,8 @@ uint32_t stream_id(int step, int kind) { return (uint32_t(step) << 8) | uint32_t
 constexpr int KIND_SWAP = 0, KIND_TRIAD_A = 1, KIND_TRIAD_X = 2, KIND_TRIAD_Y = 3,
               KIND_TRIAD_D = 4, KIND_SQ_LEFT = 5, KIND_SQ_RIGHT = 8;
 
+GemmDesc G_(const ModeIdx& m, const ModeIdx& n, const ModeIdx& k, double alpha = 1.0,
+            double beta = 0.0);
 GemmDesc G(const ModeIdx& m, const ModeIdx& n, const ModeIdx& k, double alpha = 1.0,
            double beta = 0.0) {
   GemmDesc g;
@@ -28,6 +30,33 @@ GemmDesc G(const ModeIdx& m, const ModeIdx& n, const ModeIdx& k, double alpha = 
   g.alpha = alpha;
   g.beta = beta;
   return g;
+}
+
+// Runs [a, b) of consecutive values whose gaps are <= tau times the larger value
+// (degenerate multiplets).
+std::vector<std::pair<int, int>> multiplets(const std::vector<double>& v, int n, double tau) {
+  std::vector<std::pair<int, int>> out;
+  int a = 0;
+  for (int i = 1; i <= n; ++i) {
+    if (i == n || v[i - 1] - v[i] > tau * v[i - 1]) {
+      if (i - a > 1) out.push_back({a, i});
+      a = i;
+    }
+  }
+  return out;
+}
+
+// A truncation to k values never splits a multiplet: move the cut to its first member (or,
+// when the multiplet starts at 0, keep it whole).
+int64_t multiplet_cut(const std::vector<double>& v, int64_t k, double tau) {
+  if (k <= 0 || k >= int64_t(v.size())) return k;
+  for (auto& ab : multiplets(v, int(v.size()), tau))
+    if (ab.first < k && k < ab.second) return ab.first > 0 ? ab.first : ab.second;
+  return k;
+}
+
+GemmDesc G_(const ModeIdx& m, const ModeIdx& n, const ModeIdx& k, double alpha, double beta) {
+  return G(m, n, k, alpha, beta);
 }
 
 int64_t prod(const std::vector<int64_t>& v, size_t a, size_t b) {
@@ -53,6 +82,7 @@ struct tatrg_ctx {
   uint32_t replica = 0;     // Philox counter word 2 (sweep index)
   std::vector<double> lnc;  // ln c_k, k = 0..step
   bool ready = false;
+  double tau = 1e-10;  // relative gap of a degenerate multiplet (larger in split steps)
   // last step record
   tatrg_step_info info{};
   std::vector<double> spec_s, spec_sigma;
@@ -96,6 +126,12 @@ struct tatrg_ctx {
     flip_by_sign(X, F, n, Y, F2, v.d(), stream);
   }
 
+  // Canonical basis of the columns of X (F x n): the sign rule for single columns and, for
+  // each degenerate multiplet of vals, the rotation V_M -> V_M O with O the polar factor
+  // of V_M^T W (W: hashed weights).  The same rotation is applied to Y: to its rows when
+  // y_rows (Y is n x F2), else to its columns (Y is F2 x n).
+  void canonical_cols(double* X, int64_t F, int n, const std::vector<double>& vals, double* Y,
+                      int64_t F2, bool y_rows);
   void init_ising(double beta, double h, int dd);
   void rg_step();
   void resplit_and_rotate(DMat& phi, DMat& psi, int64_t rows, int64_t Dg,
@@ -106,6 +142,37 @@ struct tatrg_ctx {
 };
 
 // ---------------------------------------------------------------------------------
+void tatrg_ctx::canonical_cols(double* X, int64_t F, int n, const std::vector<double>& vals,
+                               double* Y, int64_t F2, bool y_rows) {
+  if (y_rows) fix_sign_cols_rows(X, F, n, Y, F2);
+  else fix_sign_cols(X, F, n, Y, F2);
+  const int saved = eng.prec;
+  eng.prec = 0;
+  for (auto& ab : multiplets(vals, n, tau)) {
+    const int a = ab.first, m = ab.second - ab.first;
+    TATRG_CHECK(m <= 32, TATRG_ENUMERIC, "degenerate multiplet larger than 32");
+    DevBuf G(m * m * sizeof(double), stream), O(m * m * sizeof(double), stream);
+    multiplet_overlap(X, F, n, a, m, G.d(), stream);
+    SvdResult e = eng.svd(G.d(), m, m);
+    eng.mm(m, m, m, e.U.p(), m, false, e.V.p(), m, true, O.d(), m);  // O = U V^T
+    DevBuf T(F * m * sizeof(double), stream);
+    // X[:, a:a+m] <- X[:, a:a+m] O
+    eng.gemm(G_(modes({{F, n, m}}), modes({{m, 1, 1}}), modes({{m, 1, m}})), X + a, O.d(), T.d());
+    copy_modes(X + a, T.d(), modes({{F, m, n}, {m, 1, 1}}), 1.0, stream);
+    if (Y) {
+      DevBuf T2(F2 * m * sizeof(double), stream);
+      if (y_rows) {  // Y[a:a+m, :] <- O^T Y[a:a+m, :]
+        eng.gemm(G_(modes({{m, 1, F2}}), modes({{F2, 1, 1}}), modes({{m, m, F2}})), O.d(), Y + a * F2, T2.d());
+        copy_modes(Y + a * F2, T2.d(), modes({{m * F2, 1, 1}}), 1.0, stream);
+      } else {       // Y[:, a:a+m] <- Y[:, a:a+m] O
+        eng.gemm(G_(modes({{F2, n, m}}), modes({{m, 1, 1}}), modes({{m, 1, m}})), Y + a, O.d(), T2.d());
+        copy_modes(Y + a, T2.d(), modes({{F2, m, n}, {m, 1, 1}}), 1.0, stream);
+      }
+    }
+  }
+  eng.prec = saved;
+}
+
 void tatrg_ctx::init_ising(double beta, double h, int dd) {
   d = dd;
   const int64_t n = int64_t(1) << d;
@@ -215,7 +282,10 @@ void tatrg_ctx::rg_step() {
   TATRG_CHECK(ready, TATRG_ESTATE, "rg_step before init_ising / set_state");
   step++;
   const bool split = p.precision != TATRG_FP64 && step >= std::max(1, p.split_from_step);
-  eng.prec = split ? p.precision : 0;
+  const int mask = p.split_stages ? p.split_stages : 31;
+  tau = split ? 1e-6 : 1e-10;
+  auto stage_prec = [&](Stage sg) { eng.prec = (split && (mask >> sg) & 1) ? p.precision : 0; };
+  stage_prec(ST_SWAP);
   cudaStream_t st = stream;
   StageTimer tm(st);
   const long launches0 = eng.stats().launches, tc0 = eng.stats().tc_launches;
@@ -283,7 +353,7 @@ void tatrg_ctx::rg_step() {
     };
     sw = eng.rsvd(apply, rapply, rows, rows, ell, p.q, om.d());
   }
-  const int64_t Dg = keep_count(sw.s, 1e-14, chi());
+  const int64_t Dg = multiplet_cut(sw.s, keep_count(sw.s, 1e-14, chi()), tau);
   TATRG_CHECK(Dg >= 1, TATRG_ENUMERIC, "bond swap: zero middle tensor");
   info.swap_gap = (Dg < int64_t(sw.s.size())) ? (sw.s[Dg - 1] - sw.s[Dg]) / sw.s[0] : INFINITY;
   spec_sigma = sw.s;
@@ -300,6 +370,7 @@ void tatrg_ctx::rg_step() {
 
   // ======================== triad isometries and tensors (Eqs. 2-4) ========================
   tm.mark(1);
+  stage_prec(ST_TRIAD);
   const int64_t nx = Da_ * Gd * Ds * Dg;  // elements of X (= Y)
   DevBuf Xs(nx * sizeof(double), st), Ys(nx * sizeof(double), st);
   TATRG_CUDA(cudaMemcpyAsync(Xs.d(), X.d(), nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -369,6 +440,7 @@ void tatrg_ctx::rg_step() {
 
   // ============================ squeezers (Eq. 5) ============================
   tm.mark(2);
+  stage_prec(ST_SQUEEZE);
   std::vector<DMat> Ms(d - 1), Nts(d - 1);  // M[(a,b),k] and N^T[(a,b),k]
   std::vector<int64_t> Kn(d - 1, 0);
   spec_sq.assign(d - 1, {});
@@ -503,7 +575,7 @@ void tatrg_ctx::rg_step() {
       DevBuf C(kL * kR * sizeof(double), st);
       eng.mm(kL, kR, Pn, RtL.p(), kL, true, RtR.p(), kR, false, C.d(), kR);
       SvdResult cs = eng.svd(C.d(), kL, kR);
-      const int64_t k = keep_count(cs.s, 1e-12, chi());
+      const int64_t k = multiplet_cut(cs.s, keep_count(cs.s, 1e-12, chi()), tau);
       TATRG_CHECK(k >= 1, TATRG_ENUMERIC, "squeezer core is zero");
       spec_sq[nu - 1] = cs.s;
       DevBuf isq(k * sizeof(double), st);
@@ -522,7 +594,7 @@ void tatrg_ctx::rg_step() {
       eng.mm(Pn, k, kL, RtL.p(), kL, false, cs.U.p(), cs.U.cols, false, Nts[nu - 1].p(), k);
       scale_axis(Ms[nu - 1].p(), isq.d(), Pn, k, 1, 1, st);
       scale_axis(Nts[nu - 1].p(), isq.d(), Pn, k, 1, 1, st);
-      fix_sign_cols(Ms[nu - 1].p(), Pn, int(k), Nts[nu - 1].p(), Pn);
+      canonical_cols(Ms[nu - 1].p(), Pn, int(k), cs.s, Nts[nu - 1].p(), Pn, false);
       Kn[nu - 1] = k;
       TATRG_CUDA(cudaStreamSynchronize(st));
     }
@@ -530,6 +602,7 @@ void tatrg_ctx::rg_step() {
 
   // ============================ contraction (Eqs. 6-7) ============================
   tm.mark(3);
+  stage_prec(ST_CONTRACT);
   const int64_t Ks = Kn[d - 2];
   const int64_t Kg = g > 0 ? prod(Kn, 0, g) : 1;
   const int64_t rowsN = D0 * Kg * Ks;  // rows of Phi / Psi: (i0, k_1..k_g, k_sep)
@@ -641,6 +714,7 @@ void tatrg_ctx::rg_step() {
 
   // ============================ re-split and rotation ============================
   tm.mark(4);
+  stage_prec(ST_RESPLIT);
   std::vector<int64_t> newD(d);
   newD[0] = D0;
   for (int nu = 1; nu < d; ++nu) newD[nu] = Kn[nu - 1];
@@ -688,7 +762,7 @@ void tatrg_ctx::resplit_and_rotate(DMat& phi, DMat& psi, int64_t rows, int64_t D
   // B'[a, rot] = (Q_Psi V_k)^T
   eng.gemm(G(modes({{D0, Kr * kb, 1}, {Kr, kb, D0}}), modes({{Dn, 1, rows}}), modes({{kb, 1, cs.V.cols}})),
            qb.Q.p(), cs.V.p(), Bn.d());
-  fix_sign_cols_rows(An.d(), rows, int(Dn), Bn.d(), rows);
+  canonical_cols(An.d(), rows, int(Dn), cs.s, Bn.d(), rows, true);
   A = std::move(An);
   B = std::move(Bn);
   Da = Dn;
@@ -758,7 +832,10 @@ tatrg_status tatrg_rg_step(tatrg_ctx* ctx, int nsteps) {
   return guard(ctx, [&] {
     TATRG_CHECK(nsteps >= 0, TATRG_EINVAL, "tatrg_rg_step: negative step count");
     TATRG_CHECK(ctx->ready, TATRG_ESTATE, "tatrg_rg_step before tatrg_init_ising");
-    for (int i = 0; i < nsteps; ++i) ctx->rg_step();
+    for (int i = 0; i < nsteps; ++i) {
+      ctx->rg_step();
+      TATRG_CHECK(tc_error_flag(true) == 0, TATRG_ETIMEOUT, "a tensor-core pipeline wait timed out");
+    }
   });
 }
 
@@ -897,6 +974,10 @@ tatrg_status tatrg_contract(const tatrg_contraction* c, int precision, const dou
     Engine e(static_cast<cudaStream_t>(stream));
     e.prec = precision;
     e.gemm(g, A, B, C);
+    if (precision != 0) {
+      TATRG_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+      TATRG_CHECK(tc_error_flag(true) == 0, TATRG_ETIMEOUT, "a tensor-core pipeline wait timed out");
+    }
   });
 }
 

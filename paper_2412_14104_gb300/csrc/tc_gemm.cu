@@ -1,8 +1,537 @@
-// placeholder until the tcgen05 path lands
+// Split-precision contractions on the 5th-generation tensor cores (sm_103a).
+//
+// A float64 operand x is split into two tensor-core numbers, x = hi + lo + O(2^-22 |x|)
+// for TF32 (hi = tf32(x), lo = tf32(x - hi)) or O(2^-16 |x|) for BF16, and
+// A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 in tensor memory
+// ("3xTF32" / "BF16x3").  Flow per contraction:
+//   pack   : gather the multi-mode operand into a K-major, zero-padded [rows][K] panel of
+//            hi and lo values (one pass over HBM, coalesced writes);
+//   gemm   : 128 x BN output tile per CTA; warp 0 issues TMA loads of 64-byte K slices
+//            (SWIZZLE_64B) into a ring of shared-memory stages, one thread of warp 1
+//            issues tcgen05.mma (M = 128, N = BN) into a TMEM accumulator and frees a
+//            stage with tcgen05.commit, warps 2-5 read the accumulator with tcgen05.ld and
+//            write float64 results through the multi-mode C strides (atomic adds when K is
+//            split across CTAs);
+//   every mbarrier wait is bounded in time; a wait that runs out raises an error flag,
+//   the CTA stops issuing work, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
 #include "kernels.cuh"
+
 namespace tatrg {
-bool tc_available() { return false; }
-void gemm_tc(const GemmDesc&, const double*, const double*, double*, int, cudaStream_t, Stats*) {
-  throw Error(TATRG_ENOTIMPL, "tensor-core path not built");
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 128;
+constexpr int KSLICE = 64;  // bytes of K per stage row (one SWIZZLE_64B atom)
+constexpr int SMEM_BUDGET = 192 * 1024;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s; a CTA gives up after 4 WAIT_NS
+
+__device__ int g_tc_error;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false (and the error flag) when the deadline passes
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t deadline) {
+  while (!mbar_try_wait(bar, parity)) {
+    if (now_ns() > deadline) {
+      atomicExch(&g_tc_error, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+      "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// K-major operand tile in shared memory, 64-byte rows, SWIZZLE_64B (8-row atoms of 512 B).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFF) >> 4);  // start address, 16-byte units
+  d |= uint64_t(1) << 16;                 // leading byte offset (unused for this layout)
+  d |= uint64_t(512 >> 4) << 32;          // stride byte offset: next 8-row group
+  d |= uint64_t(1) << 46;                 // descriptor version
+  d |= uint64_t(4) << 61;                 // SWIZZLE_64B
+  return d;
+}
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t acc) {
+  if (PREC == 1) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor for kind::tf32 (A/B format 2) or kind::f16 with bf16 (format 1),
+// FP32 accumulator, both operands K-major, M = 128.
+template <int PREC, int BN>
+__device__ __forceinline__ constexpr uint32_t idesc() {
+  return (1u << 4) | (uint32_t(PREC == 1 ? 2 : 1) << 7) | (uint32_t(PREC == 1 ? 2 : 1) << 10) |
+         (uint32_t(BN >> 3) << 17) | (uint32_t(TC_BM >> 4) << 24);
+}
+
+struct TcArgs {
+  DevModes mC;  // s1 = C stride of each M mode
+  DevModes nC;  // s1 = C stride of each N mode
+  int64_t M, N;
+  int kb_per_split, nkb;
+  double alpha, beta;
+  int atomic;
+  double* C;
+};
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// 128 x 128 output tile.  The K loop is cut into chunks of KC stages; each chunk
+// accumulates in one of two TMEM buffers (columns [0,128) and [128,256)) while the eight
+// epilogue warps drain the other one into per-thread double-float (hi, lo) sums, so no FP32
+// accumulation chain in the tensor memory is longer than KC * 64 bytes of K.
+template <int PREC, int KC, int STAGES>
+__global__ void __launch_bounds__(320, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+                   const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+                   TcArgs g) {
+  constexpr int BN = TC_BN;
+  constexpr int A_TILE = TC_BM * KSLICE;  // bytes
+  constexpr int B_TILE = BN * KSLICE;
+  constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;
+  constexpr int KELEM = PREC == 1 ? KSLICE / 4 : KSLICE / 2;  // K elements per stage
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[2], acc_empty[2], fin_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int64_t col_off[BN];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = int64_t(blockIdx.x) * TC_BM, n0 = int64_t(blockIdx.y) * BN;
+  const int kb0 = blockIdx.z * g.kb_per_split;
+  const int kb1 = min(g.nkb, kb0 + g.kb_per_split);
+  const int nk = kb1 - kb0;
+  const int nchunks = (nk + KC - 1) / KC;
+  const uint64_t deadline = now_ns() + WAIT_NS * 4;  // whole-CTA bound
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 8);
+    }
+    mbar_init(&fin_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base_s)),
+                 "r"(uint32_t(2 * BN)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (warp >= 2) {  // per-column C offsets of this tile
+    for (int j = threadIdx.x - 64; j < BN; j += 256) {
+      int64_t a = 0, c = 0;
+      if (n0 + j < g.N) mode_offsets(g.nC, n0 + j, a, c);
+      col_off[j] = c;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0) {
+    if (lane == 0 && nk > 0) {
+      int issued = 0;
+      for (int i = 0; i < nk; ++i) {
+        const int s = i % STAGES, round = i / STAGES;
+        if (round > 0 && !mbar_wait(&empty_bar[s], (round - 1) & 1, deadline)) break;
+        uint8_t* st = smem + s * STAGE;
+        mbar_expect_tx(&full_bar[s], STAGE);
+        const int kx = (kb0 + i) * KELEM;
+        tma_load_2d(st, &ta_hi, &full_bar[s], kx, int(m0));
+        tma_load_2d(st + A_TILE, &ta_lo, &full_bar[s], kx, int(m0));
+        tma_load_2d(st + 2 * A_TILE, &tb_hi, &full_bar[s], kx, int(n0));
+        tma_load_2d(st + 2 * A_TILE + B_TILE, &tb_lo, &full_bar[s], kx, int(n0));
+        issued = i + 1;
+      }
+      // drain: the last loads issued into each stage must have landed before the CTA exits
+      const uint64_t drain = now_ns() + WAIT_NS;
+      for (int i = max(0, issued - STAGES); i < issued; ++i)
+        mbar_wait(&full_bar[i % STAGES], (i / STAGES) & 1, drain);
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && nk > 0) {
+      constexpr uint32_t id = idesc<PREC, BN>();
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1, use = c >> 1;
+        if (use > 0 && !mbar_wait(&acc_empty[b], (use - 1) & 1, deadline)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t acc = tmem + uint32_t(b * BN);
+        const int i_end = min(nk, (c + 1) * KC);
+        for (int i = c * KC; i < i_end; ++i) {
+          const int s = i % STAGES, round = i / STAGES;
+          if (!mbar_wait(&full_bar[s], round & 1, deadline)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + s * STAGE);
+          const uint64_t ahi = sdesc_sw64(base), alo = sdesc_sw64(base + A_TILE);
+          const uint64_t bhi = sdesc_sw64(base + 2 * A_TILE), blo = sdesc_sw64(base + 2 * A_TILE + B_TILE);
+#pragma unroll
+          for (int kk = 0; kk < KSLICE / 32; ++kk) {  // 32 bytes of K per instruction
+            const uint64_t off = uint64_t(kk * 2);
+            mma<PREC>(acc, alo + off, bhi + off, id, (i > c * KC || kk > 0) ? 1u : 0u);
+            mma<PREC>(acc, ahi + off, blo + off, id, 1u);
+            mma<PREC>(acc, ahi + off, bhi + off, id, 1u);
+          }
+          mma_commit(&empty_bar[s]);
+        }
+        if (ok) mma_commit(&acc_full[b]);
+      }
+      // drain: every MMA issued by this thread completes before TMEM is released
+      mma_commit(&fin_bar);
+      mbar_wait(&fin_bar, 0, now_ns() + WAIT_NS);
+    }
+  } else if (nk > 0) {
+    // epilogue warps 2..9: TMEM lane quarter q = warp % 4, column half h
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    float hi[64], lo[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1, use = c >> 1;
+      ok = __all_sync(0xffffffffu, (ok && mbar_wait(&acc_full[b], use & 1, deadline)) ? 1 : 0) != 0;
+      if (!ok) break;
+      tc_fence_after();
+      const uint32_t ta = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * BN + h * 64);
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        uint32_t v[32];
+        tmem_ld32(ta + uint32_t(32 * half), v);
+        if (half == 1) {  // both halves are in registers: hand the buffer back to the MMA warp
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float s, e;
+          two_sum(hi[32 * half + j], __uint_as_float(v[j]), s, e);
+          hi[32 * half + j] = s;
+          lo[32 * half + j] = __fadd_rn(lo[32 * half + j], e);
+        }
+      }
+    }
+    if (ok && (m0 + row) < g.M) {
+      int64_t roff = 0, dummy = 0;
+      mode_offsets(g.mC, m0 + row, dummy, roff);
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const int col = h * 64 + j;
+        if (n0 + col < g.N) {
+          double* p = g.C + roff + col_off[col];
+          const double x = g.alpha * (double(hi[j]) + double(lo[j]));
+          if (g.atomic) atomicAdd(p, x);
+          else *p = (g.beta != 0.0) ? x + g.beta * *p : x;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(2 * BN)));
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Operand packing: dst[r * Kp + k] for r < Rp, k < Kp, zero outside the R x K operand.
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ src, DevModes rm,
+                                                   DevModes km, int64_t R, int64_t K, int64_t Kp,
+                                                   int64_t ktiles, int64_t ntiles, void* hi,
+                                                   void* lo, int r_contig) {
+  __shared__ int64_t roff[32], koff[32];
+  __shared__ double tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = (t / ktiles) * 32, k0 = (t % ktiles) * 32;
+    __syncthreads();
+    if (ty == 0) {
+      int64_t a = 0, b = 0;
+      if (r0 + tx < R) mode_offsets(rm, r0 + tx, a, b);
+      roff[tx] = a;
+    } else if (ty == 1) {
+      int64_t a = 0, b = 0;
+      if (k0 + tx < K) mode_offsets(km, k0 + tx, a, b);
+      koff[tx] = a;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      // r-contiguous sources are read with the lanes along r, others along k
+      const int rr = r_contig ? tx : i, kk = r_contig ? i : tx;
+      double v = 0.0;
+      if (r0 + rr < R && k0 + kk < K) v = src[roff[rr] + koff[kk]];
+      tile[rr][kk] = v;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+      const int64_t r = r0 + i, k = k0 + tx;
+      if (k >= Kp) continue;
+      const double x = tile[i][tx];
+      const int64_t o = r * Kp + k;
+      if (PREC == 1) {
+        const float h = tf32_rna(__double2float_rn(x));
+        const float l = tf32_rna(__double2float_rn(x - double(h)));
+        reinterpret_cast<float*>(hi)[o] = h;
+        reinterpret_cast<float*>(lo)[o] = l;
+      } else {
+        const __nv_bfloat16 h = __double2bfloat16(x);
+        const __nv_bfloat16 l = __double2bfloat16(x - double(__bfloat162float(h)));
+        reinterpret_cast<__nv_bfloat16*>(hi)[o] = h;
+        reinterpret_cast<__nv_bfloat16*>(lo)[o] = l;
+      }
+    }
+  }
+}
+
+__global__ void scale_c_kernel(double* C, DevModes m, DevModes n, int64_t M, int64_t N, double beta) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < M * N;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    int64_t i = e / N, j = e - (e / N) * N, a, c, b, d;
+    mode_offsets(m, i, a, c);
+    mode_offsets(n, j, b, d);
+    double* p = C + c + d;
+    *p = beta == 0.0 ? 0.0 : beta * *p;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+CUtensorMap make_map(void* base, int64_t rows, int64_t kp, int esize, int box_rows, int prec) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {cuuint64_t(kp), cuuint64_t(rows)};
+  cuuint64_t strides[1] = {cuuint64_t(kp * esize)};
+  cuuint32_t box[2] = {cuuint32_t(KSLICE / esize), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, prec == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                           2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  TATRG_CHECK(r == CUDA_SUCCESS, TATRG_ECUDA, "cuTensorMapEncodeTiled failed");
+  return m;
+}
+
+template <int PREC>
+void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
+            const CUtensorMap& blo, const TcArgs& a, dim3 grid, cudaStream_t s) {
+  constexpr int STAGE = 2 * TC_BM * KSLICE + 2 * TC_BN * KSLICE;
+  constexpr int STAGES = SMEM_BUDGET / STAGE;
+  constexpr int KC = PREC == 1 ? 4 : 2;  // 64 TF32 or 64 BF16 K elements per FP32 chain
+  constexpr int SMEM = STAGES * STAGE + 1024;
+  auto k = tc_gemm_kernel<PREC, KC, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    TATRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+    attr = true;
+  }
+  k<<<grid, 320, SMEM, s>>>(ahi, alo, bhi, blo, a);
+  TATRG_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+bool tc_available() {
+  static int ok = -1;
+  if (ok < 0) {
+    int dev = 0, major = 0, minor = 0;
+    ok = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
+      ok = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
+  }
+  return ok == 1;
+}
+
+int tc_error_flag(bool reset) {
+  int h = 0;
+  cudaMemcpyFromSymbol(&h, g_tc_error, sizeof(int));
+  if (reset && h) {
+    int z = 0;
+    cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
+  }
+  return h;
+}
+
+void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int prec,
+             cudaStream_t s, Stats* st) {
+  TATRG_CHECK(prec == 1 || prec == 2, TATRG_EINVAL, "gemm_tc: precision must be TF32X3 or BF16X3");
+  TATRG_CHECK(tc_available(), TATRG_ENOTIMPL, "gemm_tc: tcgen05 path needs an sm_103 GPU");
+  const int64_t M = d.m.total(), N = d.n.total(), K = d.k.total();
+  if (M == 0 || N == 0) return;
+  check_gemm(d, A, B, C);
+  const int esize = prec == 1 ? 4 : 2;
+  const int kelem = KSLICE / esize;
+  const int BN = TC_BN;
+  const int64_t Mp = cdiv(M, TC_BM) * TC_BM, Np = cdiv(N, BN) * BN, Kp = cdiv(K, kelem) * kelem;
+  TATRG_CHECK(Mp < (int64_t(1) << 31) && Np < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: operand too large");
+  // packed operands (hi, lo) in one allocation
+  const size_t abytes = size_t(Mp) * Kp * esize, bbytes = size_t(Np) * Kp * esize;
+  DevBuf pk(2 * abytes + 2 * bbytes, s);
+  uint8_t* base = pk.as<uint8_t>();
+  void *ahi = base, *alo = base + abytes, *bhi = base + 2 * abytes, *blo = base + 2 * abytes + bbytes;
+  {
+    // A: rows = m (stride s0), k (stride s0);  B: rows = n (s0), k (s1)
+    DevModes rm = dev(d.m), km = dev(d.k);
+    const int rc = (d.m.n > 0 && d.m.s0[d.m.n - 1] == 1 && !(d.k.n > 0 && d.k.s0[d.k.n - 1] == 1)) ? 1 : 0;
+    const int64_t kt = cdiv(Kp, 32), ta = (Mp / 32) * kt;
+    const int ga = int(std::min<int64_t>(ta, 152 * 64));
+    if (prec == 1) pack_kernel<1><<<ga, dim3(32, 8), 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
+    else pack_kernel<2><<<ga, dim3(32, 8), 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
+    TATRG_CUDA(cudaGetLastError());
+    DevModes rn = dev(d.n), kn = dev(d.k);
+    for (int i = 0; i < kMaxModes; ++i) kn.s0[i] = kn.s1[i];  // B's k strides
+    const int rcb = (d.n.n > 0 && d.n.s0[d.n.n - 1] == 1 && !(d.k.n > 0 && d.k.s1[d.k.n - 1] == 1)) ? 1 : 0;
+    const int64_t tb = (Np / 32) * kt;
+    const int gb = int(std::min<int64_t>(tb, 152 * 64));
+    if (prec == 1) pack_kernel<1><<<gb, dim3(32, 8), 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
+    else pack_kernel<2><<<gb, dim3(32, 8), 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
+    TATRG_CUDA(cudaGetLastError());
+  }
+  CUtensorMap mahi = make_map(ahi, Mp, Kp, esize, TC_BM, prec);
+  CUtensorMap malo = make_map(alo, Mp, Kp, esize, TC_BM, prec);
+  CUtensorMap mbhi = make_map(bhi, Np, Kp, esize, BN, prec);
+  CUtensorMap mblo = make_map(blo, Np, Kp, esize, BN, prec);
+  const int nkb = int(Kp / kelem);
+  const int64_t tiles = (Mp / TC_BM) * (Np / BN);
+  int split = 1;
+  if (tiles < 2 * 152 && nkb >= 8) split = int(std::min<int64_t>(cdiv(2 * 152, tiles), nkb / 4));
+  split = std::max(1, std::min(split, 512));
+  const int per = int(cdiv(nkb, split));
+  split = int(cdiv(nkb, per));
+  TcArgs a;
+  a.mC = dev(d.m);
+  a.nC = dev(d.n);
+  a.M = M;
+  a.N = N;
+  a.kb_per_split = per;
+  a.nkb = nkb;
+  a.alpha = d.alpha;
+  a.beta = d.beta;
+  a.atomic = split > 1 ? 1 : 0;
+  a.C = C;
+  if (split > 1) {
+    scale_c_kernel<<<int(std::min<int64_t>(cdiv(M * N, 256), 4096)), 256, 0, s>>>(C, dev(d.m), dev(d.n), M, N, d.beta);
+    TATRG_CUDA(cudaGetLastError());
+  }
+  dim3 grid(unsigned(Mp / TC_BM), unsigned(Np / BN), unsigned(split));
+  TATRG_CHECK(grid.y <= 65535, TATRG_EINVAL, "gemm_tc: N too large for the grid");
+  if (prec == 1) launch<1>(mahi, malo, mbhi, mblo, a, grid, s);
+  else launch<2>(mahi, malo, mbhi, mblo, a, grid, s);
+  if (st) {
+    st->launches += 3 + (split > 1);
+    st->tc_launches += 1;
+    st->flops_tc += 2.0 * double(M) * double(N) * double(K);
+  }
+}
+
 }  // namespace tatrg

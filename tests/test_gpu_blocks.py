@@ -132,3 +132,54 @@ def _torch():
 def torch_empty(shape):
     import torch
     return torch.empty(shape, dtype=torch.float64, device="cuda")
+
+
+def _tc_case(torch, prec, M, N, K, mmodes, nmodes, kmodes, A, B, want, beta_C=None, beta=0.0):
+    C = _dev(torch, beta_C) if beta_C is not None else torch.zeros(want.shape, dtype=torch.float64, device="cuda")
+    tg.contract(mmodes, nmodes, kmodes, _dev(torch, A), _dev(torch, B), C, beta=beta, precision=prec)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()
+    return np.max(np.abs(got - want)) / np.max(np.abs(want))
+
+
+# relative error bound of the split products: 3xTF32 keeps 22 mantissa bits per operand and
+# accumulates in FP32; the two-term BF16 split keeps 16
+TC_TOL = {tg.TF32X3: 5e-6, tg.BF16X3: 1e-4}
+
+
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+def test_contract_tensor_core_plain(torch, prec):
+    rng = np.random.default_rng(11)
+    M, N, K = 1000, 300, 517
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    err = _tc_case(torch, prec, M, N, K, [(M, K, N)], [(N, 1, 1)], [(K, 1, N)], A, B, A @ B)
+    assert err < TC_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+def test_contract_tensor_core_multimode_beta(torch, prec):
+    """Strided (permuted) operands and output, alpha/beta, ragged tiles in M, N and K."""
+    rng = np.random.default_rng(12)
+    I, J, a, b, K, L = 37, 29, 7, 11, 13, 17
+    A = rng.standard_normal((K, I, L, a))
+    B = rng.standard_normal((b, L, J, K))
+    C0 = rng.standard_normal((a, I, b, J))
+    want = np.einsum("kila,bljk->aibj", A, B) + 0.5 * C0
+    m = [(I, L * a, b * J), (a, 1, I * b * J)]
+    n = [(J, K, 1), (b, L * J * K, J)]
+    k = [(K, I * L * a, 1), (L, a, J * K)]
+    err = _tc_case(torch, prec, I * a, J * b, K * L, m, n, k, A, B, want, beta_C=C0, beta=0.5)
+    assert err < TC_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+def test_contract_tensor_core_split_k_gram(torch, prec):
+    """A Gram Y^T Y with a long K split across CTAs (float64 atomic reduction)."""
+    rng = np.random.default_rng(13)
+    m, n = 200000, 144
+    Y = rng.standard_normal((m, n)) * (0.9 ** np.arange(n))[None, :]
+    want = Y.T @ Y
+    err = _tc_case(torch, prec, n, n, m, [(n, 1, n)], [(n, 1, 1)], [(m, n, n)], Y, Y, want)
+    # each CTA sums ~1e3 positive products in the FP32 accumulator before the FP64 reduction
+    assert err < 10 * TC_TOL[prec], err

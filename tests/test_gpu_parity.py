@@ -71,18 +71,31 @@ def test_full_run_matches_oracle(name):
     assert abs(lnz - g["lnz"]) < tol * abs(g["lnz"])
 
 
-def test_degenerate_cut_is_detected():
-    """chi = 8, h = 1e-4 cuts a four-fold multiplet of the swap spectrum at step 2: the
-    library reports the tiny gap, and the step still agrees with the oracle to the level at
-    which the oracle itself moves under a 1e-15 perturbation of its input."""
+def test_degenerate_cut_moves_to_multiplet_boundary():
+    """chi = 8, h = 1e-4: at step 2 the swap spectrum has a four-fold multiplet at
+    positions 6..9, so a cut at 8 would split it.  The cut moves to 6 on both sides and the
+    step becomes well posed: GPU and oracle agree to rounding."""
     p = trg.Params(8, 3, q=2, seed=2)
     run = trg.Run(0.1497, 1e-4, 4, p).step(1)
     ctx = tg.Context(8, 3, 2, seed=2).set_state(run.A, run.s, run.B, run.k, run.partial_lnz())
     ctx.rg_step()
     run.step()
-    assert ctx.step_info().swap_gap < 1e-10
-    assert run.infos[-1]["swap_gap"] < 1e-10
-    assert abs(ctx.step_info().lnc - run.lnc[-1]) < 1e-9
+    assert run.s.size == 6 and ctx.get_state()[1].size == 6
+    assert abs(ctx.step_info().lnc - run.lnc[-1]) < 1e-12
+
+
+def test_degenerate_multiplets_get_a_canonical_basis():
+    """chi = 24: after step 2 the re-split spectrum holds a four-fold multiplet; its basis
+    feeds the random sketch of step 3.  With the canonical basis the GPU state after two
+    steps equals the oracle's (not only its spectrum), so step 3 agrees to rounding."""
+    p = trg.Params(24, 2, q=2, seed=1)
+    run = trg.Run(0.1497, 0.0, 4, p).step(2)
+    ctx = tg.Context(24, 2, 2, seed=1).init_ising(0.1497, 0.0, 4).rg_step(2)
+    A, s, B = ctx.get_state()
+    assert np.allclose(A, run.A, atol=1e-10) and np.allclose(B, run.B, atol=1e-10)
+    ctx.rg_step()
+    run.step()
+    assert abs(ctx.step_info().lnc - run.lnc[-1]) < 1e-11
 
 
 def test_single_steps_from_shared_states():

@@ -299,3 +299,34 @@ def test_flop_counts_match_cost_formulas():
     main = 8 * r * r * chi ** 7
     lower = 4 * r * chi ** 6 + 2 * (2 * r * chi ** 5 + 2 * r * chi ** 6 + 2 * r * r * chi ** 6)
     assert delta["contract"] == main + lower
+
+
+def test_canonical_basis_is_rotation_invariant():
+    """Any orthonormal basis of a degenerate multiplet maps to the same canonical basis,
+    single columns follow the sign rule, and the rotation is orthogonal."""
+    rng = np.random.default_rng(21)
+    V, _ = np.linalg.qr(rng.standard_normal((60, 7)))
+    vals = np.array([3.0, 2.0, 2.0, 2.0, 1.5, 1.0, 1.0])
+    C1, O1 = rla.canonical_basis(V, vals, 1e-10)
+    R = np.eye(7)
+    R[1:4, 1:4], _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    R[5:7, 5:7], _ = np.linalg.qr(rng.standard_normal((2, 2)))
+    R[0, 0], R[4, 4] = -1.0, -1.0
+    C2, O2 = rla.canonical_basis(V @ R, vals, 1e-10)
+    assert np.allclose(C1, C2, atol=1e-13)
+    assert np.allclose(O1.T @ O1, np.eye(7), atol=1e-14)
+    w = rla.sign_weights(60)
+    assert w @ C1[:, 0] > 0 and w @ C1[:, 4] > 0
+    # a single column reduces to fix_sign
+    F1, _ = rla.fix_sign(V[:, :1])
+    C3, _ = rla.canonical_basis(V[:, :1], vals[:1], 1e-10)
+    assert np.array_equal(F1, C3)
+
+
+def test_multiplet_cut_never_splits():
+    vals = np.array([5.0, 4.0, 3.0, 3.0, 3.0, 2.0, 1.0])
+    assert rla.multiplet_cut(vals, 3, 1e-10) == 2
+    assert rla.multiplet_cut(vals, 5, 1e-10) == 5
+    assert rla.multiplet_cut(vals, 6, 1e-10) == 6
+    assert rla.multiplet_cut(np.array([1.0, 1.0, 0.5]), 1, 1e-10) == 2
+    assert rla.multiplets(vals, 1e-10) == [(2, 5)]
