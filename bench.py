@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the Triad-ATRG RG step (4D Ising) on GB300.
+
+Workload: chi = 48, r = 3, q = 2, beta = 0.1497, h = 1e-4, seed 2 (the chi = 48
+configuration), split precision (3xTF32, FP64 small linear algebra).  One benchmark step is
+one steady-state RG step (all legs at chi): bond-swap RSVD, triad isometries and tensors,
+squeezers, contraction, re-split and the ln Z accumulation, plus the on-device Philox
+sketches.  The first steps that grow the bond dimensions to chi are setup, untimed.
+
+Prints one JSON line.  value = whole-job RG steps/s (N GPUs run independent replicas with
+their own sketch keys: the path has no data exchange, so scaling is weak).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
+same workload (one sketch application of the chi = 48 bond swap), scaled to RG steps/s by
+the step's algorithmic flop count.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CHI, R, Q, BETA, H, SEED = 48, 3, 2, 0.1497, 1e-4, 2
+WORKLOAD = ("4D Ising Triad-ATRG, chi=48 r=3 q=2, beta=0.1497 h=1e-4, seed 2; one "
+            "steady-state RG step (legs 48^4, bond 48)")
+
+
+def step_flops(chi, r, q):
+    """Algorithmic flops of one steady-state step (swap, contraction, triad, squeezers)."""
+    return ((2 * q + 2) * 4 * r * chi ** 7 + 8 * r * r * chi ** 7 + 8 * chi ** 7
+            + 12 * r ** 4 * chi ** 6)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier_max(world, value):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------------------
+def oracle_sample(min_seconds=10.0):
+    """Time the FP64 oracle's bond-swap operator (one product Mid @ Omega of the chi = 48
+    step) on a growing number of sketch columns until it takes ~min_seconds; return
+    (seconds per RG step extrapolated by flops, description, threads)."""
+    import numpy as np
+    from oracle import trg
+    from paper_2412_14104_gb300 import synth
+    A, s, B = synth.split_state(7, (CHI,) * 4, CHI)
+    Dk, I, Da = CHI, CHI ** 3, CHI
+    As = A.reshape(Dk, I, Da) * s[None, None, :]
+    Bs = B.reshape(Da, Dk, I) * s[:, None, None]
+    op = trg.SwapOp(As, Bs, None)
+    cols = 1
+    while True:
+        om = synth.gaussian_matrix(3, Da * I, cols)
+        t = time.perf_counter()
+        op.matmul(om)
+        dt = time.perf_counter() - t
+        if dt >= min_seconds or cols >= 3 * CHI:
+            break
+        cols = min(3 * CHI, max(cols * 2, int(cols * min_seconds / max(dt, 1e-3)) + 1))
+    sample_flops = 4.0 * CHI ** 6 * cols
+    per_step = dt * step_flops(CHI, R, Q) / sample_flops
+    desc = ("oracle SwapOp.matmul (Mid @ Omega of the chi=48 bond swap) on %d sketch columns: "
+            "%.3g flop in %.2f s, scaled by the step's %.3g algorithmic flop" %
+            (cols, sample_flops, dt, step_flops(CHI, R, Q)))
+    try:
+        from threadpoolctl import threadpool_info
+        threads = max((d.get("num_threads", 0) for d in threadpool_info()), default=os.cpu_count())
+    except Exception:
+        threads = os.cpu_count()
+    return per_step, desc, threads
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(min_seconds=2.0)
+    times = []
+    desc, threads = "", os.cpu_count()
+    for _ in range(args.steps):
+        per_step, desc, threads = oracle_sample(min_seconds=max(2.0, 20.0 / max(args.steps, 1)))
+        times.append(per_step)
+    per = sum(times) / len(times)
+    value = 1.0 / per
+    line = {
+        "impl": "reference", "metric": "RG steps/s at chi=48 (split precision); TFLOP/s; df vs FP64 oracle",
+        "value": value, "unit": "RG steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "chi": CHI, "r": R, "q": Q},
+        "cpu_baseline": {"value": value, "unit": "RG steps/s", "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "RG steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------
+def delta_f_check(tg):
+    """Split-precision free energy against the stored FP64 oracle value of the chi = 24,
+    r = 2, q = 2, 40-step run (h = 0, seed 1): relative differences of ln Z / V."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_c2_chi24.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        gold = json.load(f)
+    c = gold["config"]
+    out = {"config": "chi=24 r=2 q=2 beta=0.1497 h=0 seed 1, 40 steps", "oracle_lnz": gold["lnz"]}
+    fp = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"]).init_ising(c["beta"], c["h"], c["d"])
+    out["fp64_gpu_rel"] = abs(fp.rg_step(c["steps"]).lnZ() - gold["lnz"]) / abs(gold["lnz"])
+    for s0 in (1, 11):
+        ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"], precision=tg.TF32X3,
+                         split_from_step=s0).init_ising(c["beta"], c["h"], c["d"])
+        out["tf32x3_from_step_%d_rel" % s0] = abs(ctx.rg_step(c["steps"]).lnZ() - gold["lnz"]) / abs(gold["lnz"])
+    return out
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import paper_2412_14104_gb300 as tg
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "fp64": tg.FP64}[args.precision]
+    seed = SEED + 1000 * rank
+    ctx = tg.Context(CHI, R, Q, seed=seed, precision=prec, profile=1, stream=stream)
+    ctx.init_ising(BETA, H, 4)
+    while True:  # setup: grow every leg to chi
+        ctx.rg_step()
+        if all(x == CHI for x in list(ctx.step_info().dims)[:5]):
+            break
+    for _ in range(args.warmup):
+        ctx.rg_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        ctx.rg_step()
+        i = ctx.step_info()
+        infos.append((list(i.flops), i.tc_ms, i.tc_flops, i.tc_launches, i.kernel_launches, list(i.ms)))
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = start.elapsed_time(end)
+    ms_max = barrier_max(world, ms)
+    value = args.steps * world / (ms_max / 1e3)
+    alg_flops = sum(sum(f) for f, *_ in infos)
+    tc_ms = sum(x[1] for x in infos)
+    tc_flops = sum(x[2] for x in infos)
+    tc_launches = sum(x[3] for x in infos)
+    launches = sum(x[4] for x in infos)
+    stage_ms = [sum(x[5][k] for x in infos) / len(infos) for k in range(5)]
+
+    # end to end through the C ABI with host buffers: state in from pinned host memory,
+    # one step, state out to pinned host memory
+    A, s, B = ctx.get_state()
+    pins = [torch.empty(a.shape, dtype=torch.float64).pin_memory() for a in (A, s, B)]
+    for p_, a in zip(pins, (A, s, B)):
+        p_.numpy()[...] = a
+    hA, hs, hB = (p_.numpy() for p_ in pins)
+    e2e_steps = max(1, min(2, args.steps))
+    k0 = ctx.step_info().step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(e2e_steps):
+        ctx.set_state(hA, hs, hB, k0 + j, 0.0)
+        ctx.rg_step()
+        hA, hs, hB = ctx.get_state()
+    torch.cuda.synchronize()
+    e2e_s = barrier_max(world, time.perf_counter() - t0)
+    io_bytes = 8 * (A.size + s.size + B.size)
+
+    peaks, src = measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    if prec == tg.TF32X3:
+        peak, note = bf16 * (1.1 / 2.25), "%s bf16 sustained x nominal tf32/bf16 (1.1/2.25)" % src
+    else:
+        peak, note = bf16, "%s bf16 sustained" % src
+    achieved = 3.0 * tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "tc_gemm_chi48_traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("dram_bytes_per_launch")
+
+    fp64_ms = None
+    if args.fp64_steps > 0 and prec != tg.FP64:
+        f64 = tg.Context(CHI, R, Q, seed=seed, stream=stream)
+        f64.set_state(A, s, B, k0, 0.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f64.rg_step(args.fp64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = e0.elapsed_time(e1) / args.fp64_steps
+    df = delta_f_check(tg) if (rank == 0 and not args.no_delta_f) else None
+
+    if rank != 0:
+        return
+    line = {
+        "metric": "RG steps/s at chi=48 (split precision); TFLOP/s; df vs FP64 oracle",
+        "value": value, "unit": "RG steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": WORKLOAD, "chi": CHI, "r": R, "q": Q, "precision": args.precision,
+                   "l2": "inputs larger than L2 (each step streams > 10 GB of tensors)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "tflops_algorithmic": alg_flops / (ms / 1e3) / 1e12,
+        "stage_ms": dict(zip(["swap", "triad", "squeeze", "contract", "resplit"], stage_ms)),
+        "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel (tcgen05 3-product split GEMM)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "peak_source": note, "launches": tc_launches,
+                     "avg_launch_ms": tc_ms / max(tc_launches, 1),
+                     "flops_per_launch": 3.0 * tc_flops / max(tc_launches, 1)},
+        "e2e": {"value": e2e_steps * world / e2e_s, "unit": "RG steps/s",
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "fp64_gpu_ms_per_step": fp64_ms,
+        "split_vs_fp64_speedup": (fp64_ms / (ms_max / args.steps)) if fp64_ms else None,
+        "delta_f": df,
+    }
+    if not args.no_cpu_baseline:
+        per, desc, threads = oracle_sample(min_seconds=10.0)
+        line["cpu_baseline"] = {"value": 1.0 / per, "unit": "RG steps/s", "cores": threads,
+                                "kind": "oracle", "sample": desc}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-delta-f", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -64,6 +64,8 @@ typedef struct {
   int split_stages;        /* bit mask of the stages whose large contractions use the split
                               precision: 1 swap, 2 triad, 4 squeezers, 8 contraction,
                               16 re-split; 0 means all */
+  int profile;             /* 1: bracket every tensor-core GEMM with CUDA events and report
+                              their device time in tatrg_step_info (tc_ms, tc_flops) */
 } tatrg_params;
 
 /* Create a context on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
@@ -127,6 +129,8 @@ typedef struct {
   double swap_gap;     /* (sigma_{Dg-1} - sigma_Dg) / sigma_0 at the swap cut (inf if none) */
   int tc_launches;     /* tcgen05 GEMM launches in the step */
   int kernel_launches; /* all library kernel launches in the step */
+  double tc_ms;        /* device time of those launches (needs params.profile = 1) */
+  double tc_flops;     /* their algorithmic flops, 2 M N K per contraction */
 } tatrg_step_info;
 
 tatrg_status tatrg_last_step_info(const tatrg_ctx* ctx, tatrg_step_info* out);

@@ -29,14 +29,16 @@ class Params(ctypes.Structure):
     _fields_ = [("chi", ctypes.c_int), ("r", ctypes.c_int), ("q", ctypes.c_int),
                 ("method", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("checkpoint_every", ctypes.c_int),
-                ("split_from_step", ctypes.c_int), ("split_stages", ctypes.c_int)]
+                ("split_from_step", ctypes.c_int), ("split_stages", ctypes.c_int),
+                ("profile", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int), ("dims", ctypes.c_int * 5), ("swap_exact", ctypes.c_int),
                 ("lnc", ctypes.c_double), ("flops", ctypes.c_double * 5),
                 ("ms", ctypes.c_double * 5), ("swap_gap", ctypes.c_double),
-                ("tc_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+                ("tc_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int),
+                ("tc_ms", ctypes.c_double), ("tc_flops", ctypes.c_double)]
 
 
 class Contraction(ctypes.Structure):
@@ -106,8 +108,9 @@ class Context:
     """One RG run on the current CUDA device (tatrg_ctx)."""
 
     def __init__(self, chi, r, q=2, method=TRIAD, precision=FP64, seed=0, split_from_step=0,
-                 split_stages=0, stream=None):
-        self.params = Params(chi, r, q, method, precision, seed, 4, split_from_step, split_stages)
+                 split_stages=0, profile=0, stream=None):
+        self.params = Params(chi, r, q, method, precision, seed, 4, split_from_step, split_stages,
+                             profile)
         h = ctypes.c_void_p()
         _check(lib().tatrg_create(ctypes.byref(self.params), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h

@@ -121,6 +121,53 @@ OrthResult Engine::orth(const double* Y, int64_t m, int64_t n) {
   return out;
 }
 
+Engine::MetricOrth Engine::orth_metric(const double* X, int64_t nin, int64_t w, const Op& metric) {
+  MetricOrth out;
+  const int passes = prec == 0 ? 2 : 3;
+  const double shift = prec == 0 ? 0.0 : 1e-6;
+  DevBuf G(w * w * sizeof(double), s_), Rk(w * w * sizeof(double), s_), Ri(w * w * sizeof(double), s_),
+      Racc(w * w * sizeof(double), s_), Rtmp(w * w * sizeof(double), s_);
+  DMat cur;
+  cur.buf = dalloc(nin * w, s_);
+  cur.rows = nin;
+  cur.cols = w;
+  TATRG_CUDA(cudaMemcpyAsync(cur.p(), X, nin * w * sizeof(double), cudaMemcpyDeviceToDevice, s_));
+  DMat U;
+  U.buf = dalloc(nin * w, s_);
+  U.rows = nin;
+  U.cols = w;
+  for (int pass = 0; pass < passes; ++pass) {
+    metric(cur.p(), w, U.p());
+    mm(w, w, nin, cur.p(), w, true, U.p(), w, false, G.d(), w);
+    cholesky(G.d(), int(w), Rk.d(), flag(0), pass == 0 ? shift : 0.0, s_);
+    st_.launches++;
+    if (read_flag(0) != 0) return out;  // ok = false
+    tri_inverse(Rk.d(), int(w), Ri.d(), s_);
+    st_.launches++;
+    DMat nxt;
+    nxt.buf = dalloc(nin * w, s_);
+    nxt.rows = nin;
+    nxt.cols = w;
+    mm(nin, w, w, cur.p(), w, false, Ri.d(), w, false, nxt.p(), w);
+    if (pass == 0) {
+      TATRG_CUDA(cudaMemcpyAsync(Racc.d(), Rk.d(), w * w * sizeof(double), cudaMemcpyDeviceToDevice, s_));
+    } else {
+      mm(w, w, w, Rk.d(), w, false, Racc.d(), w, false, Rtmp.d(), w);
+      std::swap(Racc, Rtmp);
+    }
+    cur = std::move(nxt);
+  }
+  metric(cur.p(), w, U.p());  // U = G V for the final basis
+  out.V = std::move(cur);
+  out.U = std::move(U);
+  out.R.buf = std::move(Racc);
+  out.R.rows = w;
+  out.R.cols = w;
+  out.k = int(w);
+  out.ok = true;
+  return out;
+}
+
 SvdResult Engine::svd(const double* A, int64_t m, int64_t n) {
   SvdResult r;
   const int64_t k = std::min(m, n);

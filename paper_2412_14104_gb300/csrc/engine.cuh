@@ -58,6 +58,18 @@ class Engine {
   // S and vectors in U (n x k).
   SvdResult rsvd_psd(const double* rho, int64_t n, int64_t ell, int q, const double* omega);
 
+  // Orthonormal basis of an implicit panel Q = L X whose rows are never formed: only the
+  // metric G = L^T L is available, as metric(V, w, U) computing U = G V for V (nin x w).
+  // CholeskyQR2 (shifted CholeskyQR3 for split precision) on the small Grams X^T G X.
+  // Returns V (the new basis is Q = L V), U = G V and R with L X = Q R; ok = false when a
+  // Cholesky factorisation breaks down (rank deficiency).
+  struct MetricOrth {
+    DMat V, U, R;
+    int k = 0;
+    bool ok = false;
+  };
+  MetricOrth orth_metric(const double* X, int64_t nin, int64_t w, const Op& metric);
+
   std::vector<double> to_host(const double* p, int64_t n);
   int read_flag(int idx = 0);
   int* flag(int idx = 0) { return flag_.as<int>() + idx; }

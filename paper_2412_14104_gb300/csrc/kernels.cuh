@@ -13,6 +13,31 @@ struct Stats {
   long tc_launches = 0;
   double flops_f64 = 0.0;
   double flops_tc = 0.0;  // algorithmic flops routed to the tensor cores
+  // optional device timing of the tensor-core kernels: pairs of events, reused
+  bool timing = false;
+  std::vector<cudaEvent_t> events;
+  size_t used = 0;
+  cudaEvent_t next_event() {
+    if (used == events.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) throw Error(TATRG_ECUDA, "cudaEventCreate failed");
+      events.push_back(e);
+    }
+    return events[used++];
+  }
+  // sum of the recorded intervals (call after a synchronise); resets the pool
+  double drain_ms() {
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, events[i], events[i + 1]) == cudaSuccess) t += ms;
+    }
+    used = 0;
+    return t;
+  }
+  ~Stats() {
+    for (auto e : events) cudaEventDestroy(e);
+  }
 };
 
 // kernels_f64.cu ----------------------------------------------------------------------

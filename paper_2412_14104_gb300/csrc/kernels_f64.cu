@@ -170,11 +170,19 @@ int stride1_first(const ModeIdx& x, bool first) {
 }
 }  // namespace
 
-void gemm_f64(const GemmDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
+void gemm_f64(const GemmDesc& d0, const double* A, const double* B, double* C, cudaStream_t s,
               Stats* st) {
+  if (d0.m.total() == 0 || d0.n.total() == 0) return;
+  check_gemm(d0, A, B, C);
+  GemmDesc d = d0;
+  if (cdiv(d0.n.total(), BN) > cdiv(d0.m.total(), BM)) {
+    // C^T = B^T A^T: the longer output dimension goes on grid.x
+    d.m = d0.n;
+    d.n = d0.m;
+    for (int i = 0; i < kMaxModes; ++i) std::swap(d.k.s0[i], d.k.s1[i]);
+    std::swap(A, B);
+  }
   const int64_t M = d.m.total(), N = d.n.total(), K = d.k.total();
-  if (M == 0 || N == 0) return;
-  check_gemm(d, A, B, C);
   GemmArgs g;
   g.m = dev(d.m);
   g.n = dev(d.n);
@@ -267,6 +275,8 @@ __global__ void gaussian_kernel(uint64_t seed, uint32_t sid, uint32_t replica, i
 void gaussian(uint64_t seed, uint32_t sid, uint32_t replica, int64_t n, double* out,
               cudaStream_t s) {
   if (n <= 0) return;
+  TATRG_CHECK(out != nullptr, TATRG_EINVAL, "gaussian: null output");
+  check_extent(out, n - 1, sizeof(double), "gaussian");
   int64_t npairs = (n + 1) / 2;
   int blocks = int(std::min<int64_t>(cdiv(npairs, 256), 152 * 32));
   gaussian_kernel<<<blocks, 256, 0, s>>>(seed, sid, replica, n, out);

@@ -7,9 +7,14 @@
 namespace tatrg {
 namespace {
 
-// Right-looking Cholesky on a global n x n workspace W (row-major, upper triangle used).
-__global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, double* W,
+// Packed upper-triangular index of (i, k), k >= i.
+__device__ __forceinline__ int tri_idx(int i, int k, int n) { return i * n - (i * (i - 1)) / 2 + (k - i); }
+
+// Right-looking Cholesky G + shift I = R^T R with the upper triangle held packed in shared
+// memory (n <= 160); R is written row-major with zeros below the diagonal.
+__global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, double* R,
                                                         int* status, double shift_rel) {
+  extern __shared__ double W[];
   __shared__ int fail;
   __shared__ double shift;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -20,59 +25,70 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, 
     shift = shift_rel * tr;
   }
   __syncthreads();
-  for (int64_t e = tid; e < int64_t(n) * n; e += nt) {
-    int i = int(e / n), k = int(e % n);
-    W[e] = (k >= i) ? G[e] + (i == k ? shift : 0.0) : 0.0;
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, k = e % n;
+    if (k >= i) W[tri_idx(i, k, n)] = G[e] + (i == k ? shift : 0.0);
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     if (tid == 0) {
-      double d = W[int64_t(j) * n + j];
+      double d = W[tri_idx(j, j, n)];
       double ref = G[int64_t(j) * n + j] + shift;
       if (!(d > 1e-14 * ref) || !(ref > 0.0)) fail = 1;
-      else W[int64_t(j) * n + j] = sqrt(d);
+      else W[tri_idx(j, j, n)] = sqrt(d);
     }
     __syncthreads();
     if (fail) break;
-    const double djj = W[int64_t(j) * n + j];
-    for (int k = j + 1 + tid; k < n; k += nt) W[int64_t(j) * n + k] /= djj;
+    const double djj = W[tri_idx(j, j, n)];
+    for (int k = j + 1 + tid; k < n; k += nt) W[tri_idx(j, k, n)] /= djj;
     __syncthreads();
     const int rem = n - j - 1;
-    const int64_t cnt = int64_t(rem) * rem;
-    for (int64_t e = tid; e < cnt; e += nt) {
-      int i = j + 1 + int(e / rem), k = j + 1 + int(e % rem);
-      if (k >= i) W[int64_t(i) * n + k] -= W[int64_t(j) * n + i] * W[int64_t(j) * n + k];
+    for (int e = tid; e < rem * rem; e += nt) {
+      int i = j + 1 + e / rem, k = j + 1 + e % rem;
+      if (k >= i) W[tri_idx(i, k, n)] -= W[tri_idx(j, i, n)] * W[tri_idx(j, k, n)];
     }
     __syncthreads();
+  }
+  for (int e = tid; e < n * n; e += nt) {
+    int i = e / n, k = e % n;
+    R[e] = (k >= i && !fail) ? W[tri_idx(i, k, n)] : 0.0;
   }
   if (tid == 0) *status = fail;
 }
 
-// Inverse of an upper-triangular matrix, row by row from the bottom; warp w handles the
-// columns c = w (mod warps) of row i, its lanes split the inner sum.
-__global__ void __launch_bounds__(1024) tri_inverse_kernel(const double* R, int n, double* X) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int64_t e = tid; e < int64_t(n) * n; e += blockDim.x) X[e] = 0.0;
-  __syncthreads();
-  for (int i = n - 1; i >= 0; --i) {
-    const double rii = R[int64_t(i) * n + i];
-    for (int c = i + warp; c < n; c += nw) {
-      double acc = 0.0;
-      for (int k = i + 1 + lane; k <= c; k += 32) acc += R[int64_t(i) * n + k] * X[int64_t(k) * n + c];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) X[int64_t(i) * n + c] = ((c == i ? 1.0 : 0.0) - acc) / rii;
-    }
-    __syncthreads();
+// Inverse of an upper-triangular matrix: column c of X = R^-1 is the back substitution
+// R x = e_c, independent of the other columns, so one warp solves one column (x in the
+// warp's slice of shared memory, the inner products split across lanes); no block-wide
+// barrier is needed.
+__global__ void __launch_bounds__(128) tri_inverse_kernel(const double* R, int n, double* X) {
+  extern __shared__ double xs[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 4 + w;
+  if (c >= n) return;
+  double* x = xs + w * n;
+  for (int i = lane; i < n; i += 32) x[i] = 0.0;
+  __syncwarp();
+  for (int i = c; i >= 0; --i) {
+    double acc = 0.0;
+    for (int k = i + 1 + lane; k <= c; k += 32) acc += R[int64_t(i) * n + k] * x[k];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) x[i] = ((i == c ? 1.0 : 0.0) - acc) / R[int64_t(i) * n + i];
+    __syncwarp();
   }
+  for (int i = lane; i < n; i += 32) X[int64_t(i) * n + c] = x[i];
 }
 
 // One-sided Jacobi SVD.  Ac: column-major m x N workspace (N = n rounded up to even, the
-// padding column is zero), Vc: column-major N x N initialised to the identity.
-__global__ void __launch_bounds__(1024) jacobi_kernel(double* Ac, int64_t m, int N, double* Vc,
+// padding column is zero), Vc: column-major N x N initialised to the identity.  The m x N
+// columns are worked on in shared memory and written back at the end; V stays in global
+// memory (L2).
+__global__ void __launch_bounds__(1024) jacobi_kernel(double* Acg, int64_t m, int N, double* Vc,
                                                       int max_sweeps, double tol, int* status) {
+  extern __shared__ double Ac[];
   __shared__ int rotated;
   __shared__ double fro2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t e = threadIdx.x; e < m * N; e += blockDim.x) Ac[e] = Acg[e];
   // Columns whose squared norm is below (4 eps)^2 ||A||_F^2 sit at the rounding floor:
   // they are treated as converged, otherwise rounding in a large-small pair keeps the
   // relative inner product above tol forever.
@@ -134,6 +150,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* Ac, int64_t m, int
     if (!rotated) break;
     __syncthreads();
   }
+  for (int64_t e = threadIdx.x; e < m * N; e += blockDim.x) Acg[e] = Ac[e];
   if (threadIdx.x == 0) *status = (sweep >= max_sweeps) ? 1 : 0;
 }
 
@@ -283,14 +300,22 @@ void cholesky(const double* G, int n, double* R, int* status_dev, double shift_r
               cudaStream_t s) {
   check_extent(G, int64_t(n) * n - 1, sizeof(double), "cholesky input");
   check_extent(R, int64_t(n) * n - 1, sizeof(double), "cholesky output");
-  cholesky_kernel<<<1, 1024, 0, s>>>(G, n, R, status_dev, shift_rel);
+  TATRG_CHECK(n >= 1 && n <= 160, TATRG_EINVAL, "cholesky: n must be <= 160");
+  const size_t sm = size_t(n) * (n + 1) / 2 * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    TATRG_CUDA(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 161 / 2 * 8));
+    attr = true;
+  }
+  cholesky_kernel<<<1, 1024, sm, s>>>(G, n, R, status_dev, shift_rel);
   TATRG_CUDA(cudaGetLastError());
 }
 
 void tri_inverse(const double* R, int n, double* Rinv, cudaStream_t s) {
   check_extent(R, int64_t(n) * n - 1, sizeof(double), "tri_inverse input");
   check_extent(Rinv, int64_t(n) * n - 1, sizeof(double), "tri_inverse output");
-  tri_inverse_kernel<<<1, 1024, 0, s>>>(R, n, Rinv);
+  TATRG_CHECK(n >= 1 && n <= 1024, TATRG_EINVAL, "tri_inverse: n must be <= 1024");
+  tri_inverse_kernel<<<(n + 3) / 4, 128, 4 * n * sizeof(double), s>>>(R, n, Rinv);
   TATRG_CUDA(cudaGetLastError());
 }
 
@@ -308,9 +333,14 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
                                                                                   ac.d(), vc.d());
   TATRG_CUDA(cudaGetLastError());
   const double tol = std::max(1e-15, 2.220446049250313e-16 * std::sqrt(double(m)));
-  if (m * N <= (int64_t(1) << 17) || N < 4) {
+  if ((m * N * 8 <= 200 * 1024 && N < 32) || N < 4) {
     int threads = 32 * std::max(1, std::min(32, N / 2));
-    jacobi_kernel<<<1, threads, 0, s>>>(ac.d(), m, N, vc.d(), 60, tol, status_dev);
+    static bool attr = false;
+    if (!attr) {
+      TATRG_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+      attr = true;
+    }
+    jacobi_kernel<<<1, threads, size_t(m * N) * sizeof(double), s>>>(ac.d(), m, N, vc.d(), 60, tol, status_dev);
     TATRG_CUDA(cudaGetLastError());
   } else {
     // tall: one block per pair and one launch per round; the host reads the rotation flag
@@ -321,11 +351,12 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
     TATRG_CUDA(cudaMemsetAsync(fro2, 0, sizeof(double), s));
     sumsq_kernel<<<int(std::min<int64_t>(cdiv(m * N, 256), 1024)), 256, 0, s>>>(ac.d(), m * N, fro2);
     TATRG_CUDA(cudaGetLastError());
+    const int thr = m >= 256 ? 256 : (m >= 128 ? 128 : 64);
     int converged = 0, sweep = 0;
     for (; sweep < 60 && !converged; ++sweep) {
       TATRG_CUDA(cudaMemsetAsync(rot, 0, sizeof(int), s));
       for (int r = 0; r < N - 1; ++r) {
-        tall_jacobi_round_kernel<<<N / 2, 256, 0, s>>>(ac.d(), m, N, vc.d(), r, tol, fro2, rot);
+        tall_jacobi_round_kernel<<<N / 2, thr, 0, s>>>(ac.d(), m, N, vc.d(), r, tol, fro2, rot);
         TATRG_CUDA(cudaGetLastError());
       }
       int h = 0;

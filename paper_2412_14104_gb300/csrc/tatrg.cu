@@ -89,7 +89,9 @@ struct tatrg_ctx {
   std::vector<std::vector<double>> spec_sq;
   double flops[ST_N] = {0, 0, 0, 0, 0};
 
-  tatrg_ctx(const tatrg_params& pp, cudaStream_t s) : p(pp), stream(s), eng(s) {}
+  tatrg_ctx(const tatrg_params& pp, cudaStream_t s) : p(pp), stream(s), eng(s) {
+    eng.stats().timing = pp.profile != 0;
+  }
 
   int64_t chi() const { return p.chi; }
   int64_t width() const { return int64_t(p.r) * p.chi; }
@@ -289,6 +291,8 @@ void tatrg_ctx::rg_step() {
   cudaStream_t st = stream;
   StageTimer tm(st);
   const long launches0 = eng.stats().launches, tc0 = eng.stats().tc_launches;
+  const double tcf0 = eng.stats().flops_tc;
+  eng.stats().drain_ms();
   for (auto& f : flops) f = 0.0;
   auto count = [&](Stage sg, const GemmDesc& g) {
     flops[sg] += 2.0 * double(g.m.total()) * double(g.n.total()) * double(g.k.total());
@@ -351,7 +355,99 @@ void tatrg_ctx::rg_step() {
           G(modes({{I, 1, w}}), modes({{Da_, w, I * w}, {w, 1, 1}}), modes({{Da_ * D0, I, Da_ * w}})),
           Bs.d(), W.d(), Z);
     };
-    sw = eng.rsvd(apply, rapply, rows, rows, ell, p.q, om.d());
+    // Compressed randomized SVD.  Mid = L R with the inner index (a, k, b):
+    //   (R x)[a,k,b] = sum_j Bs[a,k,j] x[(b,j)],  (L w)[(a,i)] = sum_{k,b} As[k,i,b] w[a,k,b];
+    // every basis of the subspace iteration lies in range(L) or range(R^T), so it is kept
+    // as Q = L V (or R^T V) and orthonormalised in the metrics L^T L = 1 (x) G_A and
+    // R R^T = G_B (x) 1, with G_A[(k,b),(k',b')] = sum_i As As and
+    // G_B[(a,k),(a',k')] = sum_j Bs Bs.  Same subspaces as the explicit iteration, without
+    // the rows x ell panels; only X and Y are formed at the end.
+    const int64_t nin = D0 * Da_;
+    const int64_t nL = Da_ * nin;  // rows of an inner panel [a][k][b]
+    bool done = false;
+    if (nL > ell) {
+      DevBuf GA(nin * nin * sizeof(double), st), GB(nin * nin * sizeof(double), st);
+      run(ST_SWAP,
+          G(modes({{D0, I * Da_, Da_ * nin}, {Da_, 1, nin}}), modes({{D0, I * Da_, Da_}, {Da_, 1, 1}}),
+            modes({{I, Da_, Da_}})),
+          As.d(), As.d(), GA.d());
+      run(ST_SWAP, G(modes({{nin, I, nin}}), modes({{nin, I, 1}}), modes({{I, 1, 1}})), Bs.d(), Bs.d(), GB.d());
+      auto metric_L = [&](const double* V, int64_t w, double* U) {  // (1 (x) G_A) V
+        run(ST_SWAP,
+            G(modes({{nin, nin, w}}), modes({{Da_, nin * w, nin * w}, {w, 1, 1}}), modes({{nin, 1, w}})),
+            GA.d(), V, U);
+      };
+      auto metric_R = [&](const double* V, int64_t w, double* U) {  // (G_B (x) 1) V
+        run(ST_SWAP, G(modes({{nin, nin, Da_ * w}}), modes({{Da_ * w, 1, 1}}), modes({{nin, 1, Da_ * w}})),
+            GB.d(), V, U);
+      };
+      auto apply_R = [&](const double* X, int64_t w, double* W) {  // W = R X
+        run(ST_SWAP,
+            G(modes({{Da_ * D0, I, Da_ * w}}), modes({{Da_, I * w, w}, {w, 1, 1}}), modes({{I, 1, w}})),
+            Bs.d(), X, W);
+      };
+      auto apply_L = [&](const double* W, int64_t w, double* Y) {  // Y = L W
+        run(ST_SWAP,
+            G(modes({{I, Da_, w}}), modes({{Da_, D0 * Da_ * w, I * w}, {w, 1, 1}}),
+              modes({{D0, I * Da_, Da_ * w}, {Da_, 1, w}})),
+            As.d(), W, Y);
+      };
+      auto apply_Rt = [&](const double* W, int64_t w, double* Z) {  // Z = R^T W
+        run(ST_SWAP,
+            G(modes({{I, 1, w}}), modes({{Da_, w, I * w}, {w, 1, 1}}), modes({{Da_ * D0, I, Da_ * w}})),
+            Bs.d(), W, Z);
+      };
+      DMat W0;
+      W0.buf = dalloc(nL * ell, st);
+      apply_R(om.d(), ell, W0.p());
+      om.release();
+      Engine::MetricOrth Qm = eng.orth_metric(W0.p(), nL, ell, metric_L);
+      bool ok = Qm.ok;
+      for (int it = 0; ok && it < p.q; ++it) {
+        Engine::MetricOrth Qt = eng.orth_metric(Qm.U.p(), nL, ell, metric_R);
+        ok = Qt.ok;
+        if (ok) {
+          Qm = eng.orth_metric(Qt.U.p(), nL, ell, metric_L);
+          ok = Qm.ok;
+        }
+      }
+      Engine::MetricOrth Pm;
+      if (ok) {
+        Pm = eng.orth_metric(Qm.U.p(), nL, ell, metric_R);  // B^T = R^T U = P R
+        ok = Pm.ok;
+      }
+      if (ok) {
+        DevBuf Rt(ell * ell * sizeof(double), st);
+        transpose(Pm.R.p(), ell, ell, Rt.d(), st);
+        SvdResult c = eng.svd(Rt.d(), ell, ell);  // R^T = W S Z^T
+        const int64_t r = c.r;
+        // explicit singular vectors: U = L (V W), V = R^T (V_P Z)
+        DMat WX, WY;
+        WX.buf = dalloc(nL * r, st);
+        WY.buf = dalloc(nL * r, st);
+        eng.mm(nL, r, ell, Qm.V.p(), ell, false, c.U.p(), c.U.cols, false, WX.p(), r);
+        eng.mm(nL, r, ell, Pm.V.p(), ell, false, c.V.p(), c.V.cols, false, WY.p(), r);
+        sw.r = int(r);
+        sw.s = c.s;
+        sw.S = std::move(c.S);
+        sw.U.buf = dalloc(rows * r, st);
+        sw.U.rows = rows;
+        sw.U.cols = r;
+        sw.V.buf = dalloc(rows * r, st);
+        sw.V.rows = rows;
+        sw.V.cols = r;
+        apply_L(WX.p(), r, sw.U.p());
+        apply_Rt(WY.p(), r, sw.V.p());
+        done = true;
+      }
+    }
+    if (!done) {
+      if (om.empty()) {
+        om = DevBuf(rows * ell * sizeof(double), st);
+        gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st);
+      }
+      sw = eng.rsvd(apply, rapply, rows, rows, ell, p.q, om.d());
+    }
   }
   const int64_t Dg = multiplet_cut(sw.s, keep_count(sw.s, 1e-14, chi()), tau);
   TATRG_CHECK(Dg >= 1, TATRG_ENUMERIC, "bond swap: zero middle tensor");
@@ -734,6 +830,8 @@ void tatrg_ctx::rg_step() {
   info.lnc = lnc.back();
   info.kernel_launches = int(eng.stats().launches - launches0);
   info.tc_launches = int(eng.stats().tc_launches - tc0);
+  info.tc_flops = eng.stats().flops_tc - tcf0;
+  info.tc_ms = eng.stats().drain_ms();
 }
 
 void tatrg_ctx::resplit_and_rotate(DMat& phi, DMat& psi, int64_t rows, int64_t Dg,
@@ -813,6 +911,14 @@ tatrg_status tatrg_create(const tatrg_params* params, void* cuda_stream, tatrg_c
                 "tatrg_create: unknown method");
     TATRG_CHECK(params->precision >= TATRG_FP64 && params->precision <= TATRG_BF16X3, TATRG_EINVAL,
                 "tatrg_create: unknown precision");
+    // The step's buffers come from the device's stream-ordered pool; keep freed blocks in
+    // the pool across synchronisations instead of returning them to the driver each time.
+    int dev = 0;
+    cudaMemPool_t pool;
+    TATRG_CUDA(cudaGetDevice(&dev));
+    TATRG_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t keep = UINT64_MAX;
+    TATRG_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
     *out = new tatrg_ctx(*params, static_cast<cudaStream_t>(cuda_stream));
   });
 }

@@ -478,7 +478,8 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   const size_t abytes = size_t(Mp) * Kp * esize, bbytes = size_t(Np) * Kp * esize;
   DevBuf pk(2 * abytes + 2 * bbytes, s);
   uint8_t* base = pk.as<uint8_t>();
-  void *ahi = base, *alo = base + abytes, *bhi = base + 2 * abytes, *blo = base + 2 * abytes + bbytes;
+  void *ahi = base, *alo = base + abytes;
+  void *bhi = base + 2 * abytes, *blo = base + 2 * abytes + bbytes;
   {
     // A: rows = m (stride s0), k (stride s0);  B: rows = n (s0), k (s1)
     DevModes rm = dev(d.m), km = dev(d.k);
@@ -488,14 +489,24 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     if (prec == 1) pack_kernel<1><<<ga, dim3(32, 8), 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
     else pack_kernel<2><<<ga, dim3(32, 8), 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
     TATRG_CUDA(cudaGetLastError());
+    // a Gram (B is A read the same way) reuses A's panels
+    bool same = (A == B) && Np == Mp && d.m.n == d.n.n && d.k.n > 0;
+    for (int i = 0; same && i < d.m.n; ++i) same = d.m.ext[i] == d.n.ext[i] && d.m.s0[i] == d.n.s0[i];
+    for (int i = 0; same && i < d.k.n; ++i) same = d.k.s0[i] == d.k.s1[i];
+    if (same) {
+      bhi = ahi;
+      blo = alo;
+    }
     DevModes rn = dev(d.n), kn = dev(d.k);
     for (int i = 0; i < kMaxModes; ++i) kn.s0[i] = kn.s1[i];  // B's k strides
     const int rcb = (d.n.n > 0 && d.n.s0[d.n.n - 1] == 1 && !(d.k.n > 0 && d.k.s1[d.k.n - 1] == 1)) ? 1 : 0;
     const int64_t tb = (Np / 32) * kt;
     const int gb = int(std::min<int64_t>(tb, 152 * 64));
-    if (prec == 1) pack_kernel<1><<<gb, dim3(32, 8), 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
-    else pack_kernel<2><<<gb, dim3(32, 8), 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
-    TATRG_CUDA(cudaGetLastError());
+    if (!same) {
+      if (prec == 1) pack_kernel<1><<<gb, dim3(32, 8), 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
+      else pack_kernel<2><<<gb, dim3(32, 8), 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
+      TATRG_CUDA(cudaGetLastError());
+    }
   }
   CUtensorMap mahi = make_map(ahi, Mp, Kp, esize, TC_BM, prec);
   CUtensorMap malo = make_map(alo, Mp, Kp, esize, TC_BM, prec);
@@ -525,8 +536,11 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   }
   dim3 grid(unsigned(Mp / TC_BM), unsigned(Np / BN), unsigned(split));
   TATRG_CHECK(grid.y <= 65535, TATRG_EINVAL, "gemm_tc: N too large for the grid");
+  const bool timed = st && st->timing;
+  if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
   if (prec == 1) launch<1>(mahi, malo, mbhi, mblo, a, grid, s);
   else launch<2>(mahi, malo, mbhi, mblo, a, grid, s);
+  if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
   if (st) {
     st->launches += 3 + (split > 1);
     st->tc_launches += 1;
