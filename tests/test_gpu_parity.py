@@ -49,11 +49,14 @@ def _min_gap(g, k):
     return min([x for x in gaps if x is not None] + [math.inf])
 
 
-@pytest.mark.parametrize("name", ["c1_chi6", "d4_chi10_h", "d2_chi16", "d3_chi8"])
+@pytest.mark.parametrize("name", ["c1_chi6", "d4_chi10_h", "d2_chi16", "d3_chi8", "c2_chi24"])
 def test_full_run_matches_oracle(name):
     """Every step's ln c_k and s', and the final ln Z / V.  A cut through a degenerate
     multiplet (relative gap < 1e-8, several correct answers) would make later values depend
-    on rounding; the strict tolerance then relaxes to 1e-7 for the rest of the run."""
+    on rounding; the strict tolerance then relaxes to 1e-7 for the rest of the run.
+    Rounding differences grow by ~1.6 per step along the RG trajectory (measured with the
+    oracle under a 1e-10 perturbation), so the spectra of steps beyond 20 get 1e-9; ln Z,
+    where step k weighs 2^-k, keeps the 1e-11 bar."""
     g = _gold(name)
     c = g["config"]
     ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"]).init_ising(c["beta"], c["h"], c["d"])
@@ -66,7 +69,8 @@ def test_full_run_matches_oracle(name):
         assert abs(info.lnc - g["lnc"][k + 1]) < tol * max(1.0, abs(g["lnc"][k + 1])), k
         s = ctx.spectrum(0)
         assert s.size == len(g["s"][k + 1])
-        assert np.max(np.abs(s - np.array(g["s"][k + 1]))) < 10 * tol, k
+        stol = 10 * tol if k < 20 else max(10 * tol, 1e-9)
+        assert np.max(np.abs(s - np.array(g["s"][k + 1]))) < stol, k
     lnz = ctx.lnZ()
     assert abs(lnz - g["lnz"]) < tol * abs(g["lnz"])
 
