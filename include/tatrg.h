@@ -180,6 +180,21 @@ tatrg_status tatrg_orth(int precision, int64_t m, int64_t n, const double* Y, do
 tatrg_status tatrg_svd(int64_t m, int64_t n, const double* A, double* U, double* S, double* V,
                        void* cuda_stream);
 
+/* The same thin SVD as tatrg_svd, for callers that cannot allocate device memory: code
+ * that runs while another allocator owns the whole device budget (a framework's caching
+ * pool, a fixed reservation), or code where the implicit synchronisation of cudaMalloc /
+ * cudaFree is not allowed.  The paper has no counterpart; this is a property of the
+ * library.  No memory is allocated: the workspace is one fixed device array of 2 MiB
+ * that every GPU loading the library keeps until the process exits, so the size limit is
+ * (m + N + 3) * N + 3 <= 262144 doubles with N = n rounded up to even (e.g. n = 144 with
+ * m <= 1670, n = 256 with m <= 762); larger inputs return TATRG_EINVAL.  The first call on
+ * a device looks up that array's device address (make it before any stream capture).  All
+ * calls share the array: calls whose work overlaps on the GPU race; each call rewrites
+ * the whole workspace it reads.  Pointers are device pointers with the layout of
+ * tatrg_svd; the call synchronises the stream.  Errors go to tatrg_last_error(NULL). */
+tatrg_status tatrg_svd_noalloc(int64_t m, int64_t n, const double* A, double* U, double* S,
+                               double* V, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,7 @@ def lib():
             "tatrg_contract": [ctypes.POINTER(Contraction), I, P, P, P, P],
             "tatrg_orth": [I, I64, I64, P, P, P, ctypes.POINTER(I), P],
             "tatrg_svd": [I64, I64, P, P, P, P, P],
+            "tatrg_svd_noalloc": [I64, I64, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -227,3 +228,12 @@ def svd(A, U, S, V, stream=None):
     _check(lib().tatrg_svd(m, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(U.data_ptr()),
                            ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
                            _stream_ptr(stream)))
+
+
+def svd_noalloc(A, U, S, V, stream=None):
+    """tatrg_svd_noalloc: the same SVD with its workspace in the library's fixed device
+    array instead of allocated memory (for callers that cannot allocate)."""
+    m, n = A.shape
+    _check(lib().tatrg_svd_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(U.data_ptr()),
+                                   ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                   _stream_ptr(stream)))

@@ -75,6 +75,10 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
                 int* status_dev, cudaStream_t s, Stats* st);
 // C (n x n) = A (n x n) * B (n x n), all row-major, small FP64 helper
 void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStream_t s);
+// The same SVD with its workspace in a fixed file-scope device array (no allocation);
+// synchronises the stream.
+void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S, double* V,
+                        cudaStream_t s);
 
 // tc_gemm.cu --------------------------------------------------------------------------
 // Split-precision tcgen05 GEMM on multi-mode operands: prec 1 = 3xTF32, 2 = BF16x3.

@@ -379,6 +379,102 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
   if (st) st->launches += 5;
 }
 
+// ---------------------------------------------------------------------------------
+// Jacobi SVD without device allocation.
+//
+// Its whole workspace (the column-major copy of A, the accumulated V, the column norms and
+// ranks, the rotation and convergence flags) lives in one file-scope device array of
+// kSvdScratchDoubles doubles (2 MiB), which every GPU that loads this library keeps until
+// the process exits.  Host code may not hand the array's name to a kernel (on the host it
+// is only a stand-in for the device symbol), so the device address is looked up once per
+// device with cudaGetSymbolAddress, on the first call made with that device current.
+// All calls share the array: concurrent calls whose work overlaps on the GPU race, and
+// each call rewrites every part it reads before reading it.
+namespace {
+constexpr int64_t kSvdScratchDoubles = int64_t(1) << 18;
+static __device__ __align__(256) double g_svd_scratch[kSvdScratchDoubles];
+
+std::mutex g_svd_scratch_mu;
+std::map<int, double*> g_svd_scratch_addr;  // device ordinal -> device address
+
+double* svd_scratch_address() {
+  int dev = 0;
+  TATRG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_svd_scratch_mu);
+  auto it = g_svd_scratch_addr.find(dev);
+  if (it != g_svd_scratch_addr.end()) return it->second;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_svd_scratch);
+  TATRG_CHECK(e == cudaSuccess && p != nullptr, TATRG_ECUDA,
+              std::string("cudaGetSymbolAddress(svd scratch): ") + cudaGetErrorString(e));
+  g_svd_scratch_addr[dev] = static_cast<double*>(p);
+  return static_cast<double*>(p);
+}
+}  // namespace
+
+int64_t svd_noalloc_scratch_needed(int64_t m, int n) {
+  const int64_t N = n + (n & 1);
+  // A copy, V, column norms, ranks (as doubles), ||A||_F^2, rotation flag, status
+  return m * N + N * N + N + N + 3;
+}
+
+void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S, double* V,
+                        cudaStream_t s) {
+  TATRG_CHECK(m >= n && n >= 1 && n <= 1024, TATRG_EINVAL, "svd_noalloc: need m >= n, 1 <= n <= 1024");
+  const int64_t need = svd_noalloc_scratch_needed(m, n);
+  TATRG_CHECK(need <= kSvdScratchDoubles, TATRG_EINVAL,
+              "svd_noalloc: m x n too large for the fixed scratch (needs (m + n + 3) * n + 3 "
+              "<= 262144 doubles for even n)");
+  double* base = svd_scratch_address();
+  const int N = n + (n & 1);
+  double* ac = base;
+  double* vc = ac + m * N;
+  double* sig = vc + int64_t(N) * N;
+  int* rk = reinterpret_cast<int*>(sig + N);
+  double* fro2 = sig + 2 * N;
+  int* rot = reinterpret_cast<int*>(fro2 + 1);
+  int* status = reinterpret_cast<int*>(fro2 + 2);
+  int64_t tot = m * N + int64_t(N) * N;
+  to_colmajor_kernel<<<int(std::min<int64_t>(cdiv(tot, 256), 2048)), 256, 0, s>>>(A, m, n, N, ac, vc);
+  TATRG_CUDA(cudaGetLastError());
+  const double tol = std::max(1e-15, 2.220446049250313e-16 * std::sqrt(double(m)));
+  int converged = 0;
+  if ((m * N * 8 <= 200 * 1024 && N < 32) || N < 4) {
+    int threads = 32 * std::max(1, std::min(32, N / 2));
+    TATRG_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    jacobi_kernel<<<1, threads, size_t(m * N) * sizeof(double), s>>>(ac, m, N, vc, 60, tol, status);
+    TATRG_CUDA(cudaGetLastError());
+    int h = 1;
+    TATRG_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TATRG_CUDA(cudaStreamSynchronize(s));
+    converged = (h == 0);
+  } else {
+    TATRG_CUDA(cudaMemsetAsync(fro2, 0, sizeof(double), s));
+    sumsq_kernel<<<int(std::min<int64_t>(cdiv(m * N, 256), 1024)), 256, 0, s>>>(ac, m * N, fro2);
+    TATRG_CUDA(cudaGetLastError());
+    const int thr = m >= 256 ? 256 : (m >= 128 ? 128 : 64);
+    for (int sweep = 0; sweep < 60 && !converged; ++sweep) {
+      TATRG_CUDA(cudaMemsetAsync(rot, 0, sizeof(int), s));
+      for (int r = 0; r < N - 1; ++r) {
+        tall_jacobi_round_kernel<<<N / 2, thr, 0, s>>>(ac, m, N, vc, r, tol, fro2, rot);
+        TATRG_CUDA(cudaGetLastError());
+      }
+      int h = 0;
+      TATRG_CUDA(cudaMemcpyAsync(&h, rot, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TATRG_CUDA(cudaStreamSynchronize(s));
+      converged = (h == 0);
+    }
+  }
+  TATRG_CHECK(converged, TATRG_ENUMERIC, "svd_noalloc: Jacobi SVD did not converge");
+  col_norms_kernel<<<n, 256, 0, s>>>(ac, m, sig);
+  rank_kernel<<<1, 1024, 0, s>>>(sig, n, rk, S);
+  int64_t tot2 = m * n + int64_t(n) * n;
+  svd_scatter_kernel<<<int(std::min<int64_t>(cdiv(tot2, 256), 152 * 16)), 256, 0, s>>>(ac, m, n, N, vc,
+                                                                                       sig, rk, U, V);
+  TATRG_CUDA(cudaGetLastError());
+  TATRG_CUDA(cudaStreamSynchronize(s));
+}
+
 void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStream_t s) {
   if (rows == 0 || cols == 0) return;
   check_extent(A, rows * cols - 1, sizeof(double), "transpose input");

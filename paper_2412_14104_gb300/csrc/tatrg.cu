@@ -1115,4 +1115,13 @@ tatrg_status tatrg_svd(int64_t m, int64_t n, const double* A, double* U, double*
   });
 }
 
+tatrg_status tatrg_svd_noalloc(int64_t m, int64_t n, const double* A, double* U, double* S, double* V,
+                               void* stream) {
+  return guard(nullptr, [&] {
+    TATRG_CHECK(A && U && S && V, TATRG_EINVAL, "tatrg_svd_noalloc: null argument");
+    TATRG_CHECK(n >= 1 && n <= 1024 && m >= n, TATRG_EINVAL, "tatrg_svd_noalloc: need m >= n, 1 <= n <= 1024");
+    jacobi_svd_noalloc(A, m, int(n), U, S, V, static_cast<cudaStream_t>(stream));
+  });
+}
+
 }  // extern "C"
