@@ -2,7 +2,11 @@
 // CholeskyQR2), inverse of the triangular factor, and the one-sided (Hestenes) Jacobi SVD
 // used for every core SVD / PSD eigenproblem of the RG step (swap core, triad Gram
 // eigenvectors, squeezer factors and core, re-split).
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace tatrg {
 namespace {
@@ -286,6 +290,84 @@ __global__ void __launch_bounds__(256) tall_jacobi_round_kernel(double* Ac, int6
   }
 }
 
+// The same rotations as tall_jacobi_round_kernel, all sweeps in one cooperative launch:
+// block b handles pairs b, b + gridDim.x, ... of each round and a grid-wide barrier
+// separates rounds.  All blocks decide convergence from the same flag after a barrier.
+__global__ void __launch_bounds__(256) coop_jacobi_kernel(double* Ac, int64_t m, int N, double* Vc,
+                                                          double tol, const double* fro2,
+                                                          int* rotated, int* status,
+                                                          int max_sweeps) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[3][8];
+  __shared__ double cs[2];
+  __shared__ int doit;
+  const double floor2 = 7.9e-31 * (*fro2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int sweep = 0, converged = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int r = 0; r < N - 1; ++r) {
+      for (int k = blockIdx.x; k < N / 2; k += gridDim.x) {
+        int p, q;
+        if (k == 0) { p = N - 1; q = r % (N - 1); }
+        else { p = (r + k) % (N - 1); q = (r + N - 1 - k) % (N - 1); }
+        double* ap = Ac + int64_t(p) * m;
+        double* aq = Ac + int64_t(q) * m;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+          double x = ap[i], y = aq[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga = fma(x, y, ga);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (lane == 0) { red[0][warp] = al; red[1][warp] = be; red[2][warp] = ga; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          al = be = ga = 0.0;
+          for (int w = 0; w < int(blockDim.x >> 5); ++w) { al += red[0][w]; be += red[1][w]; ga += red[2][w]; }
+          doit = (al > floor2 && be > floor2 && fabs(ga) > tol * sqrt(al) * sqrt(be)) ? 1 : 0;
+          if (doit) {
+            double zeta = (be - al) / (2.0 * ga);
+            double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            double c = 1.0 / sqrt(1.0 + t * t);
+            cs[0] = c;
+            cs[1] = c * t;
+            atomicExch(rotated, 1);
+          }
+        }
+        __syncthreads();
+        if (doit) {
+          const double c = cs[0], sn = cs[1];
+          for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+            double x = ap[i], y = aq[i];
+            ap[i] = c * x - sn * y;
+            aq[i] = sn * x + c * y;
+          }
+          double* vp = Vc + int64_t(p) * N;
+          double* vq = Vc + int64_t(q) * N;
+          for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            double x = vp[i], y = vq[i];
+            vp[i] = c * x - sn * y;
+            vq[i] = sn * x + c * y;
+          }
+        }
+        __syncthreads();
+      }
+      grid.sync();
+    }
+    const int any = atomicAdd(rotated, 0);
+    grid.sync();  // every block has read the flag
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rotated = 0;
+    grid.sync();
+    if (!any) { converged = 1; break; }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *status = converged ? 0 : 1;
+}
+
 __global__ void sumsq_kernel(const double* x, int64_t n, double* out) {
   double acc = 0.0;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n;
@@ -351,23 +433,23 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
     TATRG_CUDA(cudaMemsetAsync(fro2, 0, sizeof(double), s));
     sumsq_kernel<<<int(std::min<int64_t>(cdiv(m * N, 256), 1024)), 256, 0, s>>>(ac.d(), m * N, fro2);
     TATRG_CUDA(cudaGetLastError());
-    const int thr = m >= 256 ? 256 : (m >= 128 ? 128 : 64);
-    int converged = 0, sweep = 0;
-    for (; sweep < 60 && !converged; ++sweep) {
-      TATRG_CUDA(cudaMemsetAsync(rot, 0, sizeof(int), s));
-      for (int r = 0; r < N - 1; ++r) {
-        tall_jacobi_round_kernel<<<N / 2, thr, 0, s>>>(ac.d(), m, N, vc.d(), r, tol, fro2, rot);
-        TATRG_CUDA(cudaGetLastError());
-      }
-      int h = 0;
-      TATRG_CUDA(cudaMemcpyAsync(&h, rot, sizeof(int), cudaMemcpyDeviceToHost, s));
-      TATRG_CUDA(cudaStreamSynchronize(s));
-      converged = (h == 0);
-      if (st) st->launches += N - 1;
-    }
-    int flag = converged ? 0 : 1;
-    TATRG_CUDA(cudaMemcpyAsync(status_dev, &flag, sizeof(int), cudaMemcpyHostToDevice, s));
-    TATRG_CUDA(cudaStreamSynchronize(s));
+    // all sweeps in one cooperative launch (the blocks are co-resident by construction)
+    int thr = m >= 256 ? 256 : (m >= 128 ? 128 : 64);
+    int dev = 0, sms = 0, per_sm = 0;
+    TATRG_CUDA(cudaGetDevice(&dev));
+    TATRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TATRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_jacobi_kernel, thr, 0));
+    const int blocks = std::max(1, std::min(N / 2, per_sm * sms));
+    TATRG_CUDA(cudaMemsetAsync(rot, 0, sizeof(int), s));
+    int max_sweeps = 60;
+    double tol_ = tol;
+    double* acp = ac.d();
+    double* vcp = vc.d();
+    int64_t m_ = m;
+    int N_ = N;
+    void* args[] = {&acp, &m_, &N_, &vcp, &tol_, &fro2, &rot, &status_dev, &max_sweeps};
+    TATRG_CUDA(cudaLaunchCooperativeKernel((void*)coop_jacobi_kernel, dim3(blocks), dim3(thr), args, 0, s));
+    if (st) st->launches += 1;
   }
   DevBuf sig(n * sizeof(double), s), rk(n * sizeof(int), s);
   col_norms_kernel<<<n, 256, 0, s>>>(ac.d(), m, sig.d());
