@@ -22,6 +22,14 @@
 namespace tatrg {
 namespace {
 
+// stages (64-byte K slices) accumulated in one FP32 chain before a drain
+#ifndef TATRG_KC_TF32
+#define TATRG_KC_TF32 4
+#endif
+#ifndef TATRG_KC_BF16
+#define TATRG_KC_BF16 2
+#endif
+
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 128;
 constexpr int KSLICE = 64;  // bytes of K per stage row (one SWIZZLE_64B atom)
@@ -139,6 +147,7 @@ struct TcArgs {
   DevModes nC;  // s1 = C stride of each N mode
   int64_t M, N;
   int kb_per_split, nkb;
+  int mtiles, ntiles;  // output tiles; blockIdx.x walks them in groups of GROUP_M rows
   double alpha, beta;
   int atomic;
   double* C;
@@ -172,8 +181,20 @@ __global__ void __launch_bounds__(320, 1)
   __shared__ int64_t col_off[BN];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = int64_t(blockIdx.x) * TC_BM, n0 = int64_t(blockIdx.y) * BN;
-  const int kb0 = blockIdx.z * g.kb_per_split;
+  // grouped raster: GROUP_M consecutive row panels sweep all column panels together, so
+  // the CTAs resident at one time share a few A and B panels that stay in L2
+  int mt, nt;
+  {
+    constexpr int GROUP_M = 8;
+    const int b = blockIdx.x;
+    const int per_group = GROUP_M * g.ntiles;
+    const int first = (b / per_group) * GROUP_M;
+    const int gsize = min(g.mtiles - first, GROUP_M);
+    mt = first + (b % per_group) % gsize;
+    nt = (b % per_group) / gsize;
+  }
+  const int64_t m0 = int64_t(mt) * TC_BM, n0 = int64_t(nt) * BN;
+  const int kb0 = blockIdx.y * g.kb_per_split;
   const int kb1 = min(g.nkb, kb0 + g.kb_per_split);
   const int nk = kb1 - kb0;
   const int nchunks = (nk + KC - 1) / KC;
@@ -425,7 +446,7 @@ void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& b
             const CUtensorMap& blo, const TcArgs& a, dim3 grid, cudaStream_t s) {
   constexpr int STAGE = 2 * TC_BM * KSLICE + 2 * TC_BN * KSLICE;
   constexpr int STAGES = SMEM_BUDGET / STAGE;
-  constexpr int KC = PREC == 1 ? 4 : 2;  // 64 TF32 or 64 BF16 K elements per FP32 chain
+  constexpr int KC = PREC == 1 ? TATRG_KC_TF32 : TATRG_KC_BF16;  // stages per FP32 chain
   constexpr int SMEM = STAGES * STAGE + 1024;
   auto k = tc_gemm_kernel<PREC, KC, STAGES>;
   static bool attr = false;
@@ -534,8 +555,11 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     scale_c_kernel<<<int(std::min<int64_t>(cdiv(M * N, 256), 4096)), 256, 0, s>>>(C, dev(d.m), dev(d.n), M, N, d.beta);
     TATRG_CUDA(cudaGetLastError());
   }
-  dim3 grid(unsigned(Mp / TC_BM), unsigned(Np / BN), unsigned(split));
-  TATRG_CHECK(grid.y <= 65535, TATRG_EINVAL, "gemm_tc: N too large for the grid");
+  a.mtiles = int(Mp / TC_BM);
+  a.ntiles = int(Np / BN);
+  TATRG_CHECK(int64_t(a.mtiles) * a.ntiles < (int64_t(1) << 31) && split <= 65535, TATRG_EINVAL,
+              "gemm_tc: too many output tiles for the grid");
+  dim3 grid(unsigned(a.mtiles) * unsigned(a.ntiles), unsigned(split));
   const bool timed = st && st->timing;
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
   if (prec == 1) launch<1>(mahi, malo, mbhi, mblo, a, grid, s);
