@@ -66,6 +66,7 @@ typedef struct {
                               16 re-split; 0 means all */
   int profile;             /* 1: bracket every tensor-core GEMM with CUDA events and report
                               their device time in tatrg_step_info (tc_ms, tc_flops) */
+  int sweep_workers;       /* temperatures tatrg_sweep runs concurrently (0: 8) */
 } tatrg_params;
 
 /* Create a context on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
@@ -98,8 +99,11 @@ tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh,
                         double* d2lnZ_dbeta2 /* nullable */);
 
 /* Independent runs over `nbeta` temperatures (host array `betas`), each `nsteps` steps
- * with the sketch replica index equal to its position in the array; writes ln Z / V for
- * each to the host array `lnZ_out`.  The context's own state is left untouched. */
+ * with the sketch replica index equal to its position in the array (so each result
+ * equals a single run with that replica); writes ln Z / V for each to the host array
+ * `lnZ_out`.  params.sweep_workers host threads run temperatures concurrently, each on
+ * its own stream and device buffers.  The context's own state is left untouched.
+ * Synchronises.  The first error of any run is returned. */
 tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double h, int d,
                          int nsteps, double* lnZ_out);
 

@@ -193,7 +193,9 @@ SvdResult Engine::svd(const double* A, int64_t m, int64_t n) {
   }
   r.r = int(k);
   r.s = to_host(r.S.d(), k);
-  TATRG_CHECK(read_flag(1) == 0, TATRG_ENUMERIC, "Jacobi SVD did not converge");
+  const int jst = read_flag(1);
+  TATRG_CHECK(jst != 2, TATRG_ETIMEOUT, "Jacobi SVD: a grid barrier timed out");
+  TATRG_CHECK(jst == 0, TATRG_ENUMERIC, "Jacobi SVD did not converge");
   for (double x : r.s) TATRG_CHECK(std::isfinite(x), TATRG_ENUMERIC, "non-finite singular value");
   return r;
 }

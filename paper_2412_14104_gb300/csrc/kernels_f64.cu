@@ -9,7 +9,8 @@ namespace tatrg {
 // Multi-mode FP64 GEMM.  64x64 output tile, K tile of 16, 256 threads with a 4x4
 // register tile each; operand offsets for the tile's rows / columns / k slice are
 // decomposed once into shared memory, so arbitrary mode strides cost one table lookup
-// per element load.  gridDim.z splits K; split partial sums are added atomically.
+// per element load.  gridDim.z splits K; each split writes its partial tile to a workspace
+// and a second kernel adds the splits in order, so results do not depend on scheduling.
 namespace {
 constexpr int BM = 64, BN = 64, BK = 16;
 
@@ -22,6 +23,7 @@ struct GemmArgs {
   const double* A;
   const double* B;
   double* C;
+  double* W;  // split > 1: split x M x N row-major partials
 };
 
 __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
@@ -137,15 +139,34 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmArgs g) {
     for (int j = 0; j < 4; ++j) {
       int nn = tx + 16 * j;
       if (n0 + nn >= g.N) continue;
-      double* c = g.C + offCm[mm] + offCn[nn];
-      double v = g.alpha * acc[i][j];
       if (g.split > 1) {
-        atomicAdd(c, v);
+        g.W[(int64_t(blockIdx.z) * g.M + m0 + mm) * g.N + n0 + nn] = acc[i][j];
       } else {
+        double* c = g.C + offCm[mm] + offCn[nn];
+        double v = g.alpha * acc[i][j];
         if (g.beta != 0.0) v += g.beta * *c;
         *c = v;
       }
     }
+  }
+}
+
+// C[m, n] = alpha * sum_z W[z, m, n] (z in order) + beta * C[m, n], C through its modes
+__global__ void split_reduce_kernel(const double* W, int split, double* C, DevModes m, DevModes n,
+                                    int64_t M, int64_t N, double alpha, double beta) {
+  const int64_t total = M * N;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t i = e / N, j = e - (e / N) * N;
+    double acc = 0.0;
+    for (int z = 0; z < split; ++z) acc += W[int64_t(z) * total + e];
+    int64_t a, c, b, d;
+    mode_offsets(m, i, a, c);
+    mode_offsets(n, j, b, d);
+    double* p = C + c + d;
+    double v = alpha * acc;
+    if (beta != 0.0) v += beta * *p;
+    *p = v;
   }
 }
 
@@ -209,22 +230,32 @@ void gemm_f64(const GemmDesc& d0, const double* A, const double* B, double* C, c
   if (K == 0) { split = 1; kchunk = 0; }
   g.split = split;
   g.kchunk = kchunk;
-  if (split > 1 || K == 0) {
-    DevModes mm = dev(d.m), nn = dev(d.n);
-    // scale C by beta first (split partial sums then accumulate atomically)
-    DevModes mc = mm, nc = nn;
-    for (int i = 0; i < kMaxModes; ++i) { mc.s0[i] = mm.s1[i]; mc.s1[i] = mm.s1[i]; }
-    for (int i = 0; i < kMaxModes; ++i) { nc.s0[i] = nn.s1[i]; nc.s1[i] = nn.s1[i]; }
-    int blocks = int(std::min<int64_t>(cdiv(M * N, 256), 4096));
-    scale_modes_kernel<<<blocks, 256, 0, s>>>(C, mc, nc, M, N, d.beta);
+  g.W = nullptr;
+  // C's offsets alone, for the kernels that address only C
+  DevModes mc = dev(d.m), nc = dev(d.n);
+  for (int i = 0; i < kMaxModes; ++i) { mc.s0[i] = mc.s1[i]; nc.s0[i] = nc.s1[i]; }
+  const int rblocks = int(std::min<int64_t>(cdiv(M * N, 256), 4096));
+  if (K == 0) {
+    scale_modes_kernel<<<rblocks, 256, 0, s>>>(C, mc, nc, M, N, d.beta);
+    TATRG_CUDA(cudaGetLastError());
     if (st) st->launches++;
-    if (K == 0) return;
+    return;
+  }
+  DevBuf work;
+  if (split > 1) {
+    work.alloc(size_t(split) * size_t(M) * size_t(N) * sizeof(double), s);
+    g.W = work.d();
   }
   dim3 grid(unsigned(cdiv(M, BM)), unsigned(cdiv(N, BN)), unsigned(split));
   TATRG_CHECK(grid.y <= 65535 && cdiv(M, BM) < (int64_t(1) << 31), TATRG_EINVAL,
               "gemm_f64: problem too large for the grid");
   gemm_f64_kernel<<<grid, 256, 0, s>>>(g);
   TATRG_CUDA(cudaGetLastError());
+  if (split > 1) {
+    split_reduce_kernel<<<rblocks, 256, 0, s>>>(g.W, split, C, mc, nc, M, N, d.alpha, d.beta);
+    TATRG_CUDA(cudaGetLastError());
+    if (st) st->launches++;
+  }
   if (st) {
     st->launches++;
     st->flops_f64 += 2.0 * double(M) * double(N) * double(K);
@@ -319,21 +350,41 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   return h;
 }
 
-// v[a] += sum_f w_f X[f, a] for row-major X (F x n); w_f = (fmix32(f+1)+0.5)/2^32 - 0.5
-__global__ void weighted_colsum_kernel(const double* X, int64_t F, int n, double* v) {
-  extern __shared__ double part[];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) part[i] = 0.0;
-  __syncthreads();
-  const int64_t total = F * n;
-  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < total;
-       e += int64_t(gridDim.x) * blockDim.x) {
-    int64_t f = e / n;
-    int a = int(e - f * n);
-    double w = (double(fmix32(uint32_t(f + 1))) + 0.5) * (1.0 / 4294967296.0) - 0.5;
-    atomicAdd(&part[a], w * X[e]);
+// Per-block partials of v[a] = sum_f w_f X[f, a] for row-major X (F x n) with
+// w_f = (fmix32(f+1)+0.5)/2^32 - 0.5: block b takes rows [b*rows, (b+1)*rows), thread a
+// adds its column in row order (consecutive threads read consecutive addresses).
+__global__ void weighted_colsum_kernel(const double* X, int64_t F, int n, int64_t rows,
+                                       double* part) {
+  const int64_t f0 = int64_t(blockIdx.x) * rows, f1 = min(F, f0 + rows);
+  for (int a = threadIdx.x; a < n; a += blockDim.x) {
+    double acc = 0.0;
+    for (int64_t f = f0; f < f1; ++f) {
+      const double w = (double(fmix32(uint32_t(f + 1))) + 0.5) * (1.0 / 4294967296.0) - 0.5;
+      acc = fma(w, X[f * n + a], acc);
+    }
+    part[int64_t(blockIdx.x) * n + a] = acc;
   }
+}
+
+// out[j] = sum_b part[b * width + j], b in order
+__global__ void finish_partials_kernel(const double* part, int nb, int width, double* out) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < width; j += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) acc += part[int64_t(b) * width + j];
+    out[j] = acc;
+  }
+}
+
+// Sum of one value per thread over the block in a fixed order; the result is valid in
+// thread 0.  red holds 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&v[i], part[i]);
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[w];
+  return t;
 }
 
 // flip columns a of X (F x n, row-major) and rows a of Y (n x G) where v[a] < 0
@@ -353,40 +404,39 @@ __global__ void flip_kernel(double* X, int64_t F, int n, double* Y, int64_t G,
   }
 }
 
-// G[i, j] += sum_f X[f, a + i] w_j(f) for row-major X (F x n), i, j < m (m <= 32), with
-// w_j(f) = (fmix32((f + 1) xor (j * 0x9E3779B9)) + 0.5) / 2^32 - 0.5.
+// Per-block partials of G[i, j] = sum_f X[f, a + i] w_j(f) for row-major X (F x n),
+// i, j < m (m <= 32), with w_j(f) = (fmix32((f + 1) xor (j * 0x9E3779B9)) + 0.5) / 2^32 - 0.5.
+// Block b takes rows [b*rows, (b+1)*rows); thread (i, j) adds in row order.
 __global__ void multiplet_overlap_kernel(const double* X, int64_t F, int n, int a, int m,
-                                         double* G) {
-  __shared__ double part[32 * 32];
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) part[i] = 0.0;
-  __syncthreads();
-  for (int64_t f = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; f < F;
-       f += int64_t(gridDim.x) * blockDim.x) {
-    double w[32];
-    for (int j = 0; j < m; ++j)
-      w[j] = (double(fmix32(uint32_t(f + 1) ^ (uint32_t(j) * 0x9E3779B9u))) + 0.5) *
-                 (1.0 / 4294967296.0) - 0.5;
-    for (int i = 0; i < m; ++i) {
-      const double x = X[f * n + a + i];
-      for (int j = 0; j < m; ++j) atomicAdd(&part[i * m + j], x * w[j]);
+                                         int64_t rows, double* part) {
+  const int64_t f0 = int64_t(blockIdx.x) * rows, f1 = min(F, f0 + rows);
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t / m, j = t - (t / m) * m;
+    double acc = 0.0;
+    for (int64_t f = f0; f < f1; ++f) {
+      const double w = (double(fmix32(uint32_t(f + 1) ^ (uint32_t(j) * 0x9E3779B9u))) + 0.5) *
+                           (1.0 / 4294967296.0) - 0.5;
+      acc = fma(X[f * n + a + i], w, acc);
     }
+    part[int64_t(blockIdx.x) * m * m + t] = acc;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < m * m; i += blockDim.x) atomicAdd(&G[i], part[i]);
 }
 
-__global__ void sum_kernel(const double* x, int64_t n, double* out) {
+// per-block partial sums of x (grid-stride, fixed order)
+__global__ void sum_kernel(const double* x, int64_t n, double* part) {
+  __shared__ double red[32];
   double acc = 0.0;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n;
        e += int64_t(gridDim.x) * blockDim.x)
     acc += x[e];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// tTr = sum_a s_a sum_f A[f, a] B[a, f]
+// per-block partials of tTr = sum_a s_a sum_f A[f, a] B[a, f]
 __global__ void trace_kernel(const double* A, const double* s, const double* B, int64_t F,
-                             int Da, double* out) {
+                             int Da, double* part) {
+  __shared__ double red[32];
   double acc = 0.0;
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < F * Da;
        e += int64_t(gridDim.x) * blockDim.x) {
@@ -394,12 +444,10 @@ __global__ void trace_kernel(const double* A, const double* s, const double* B, 
     int a = int(e - f * Da);
     acc += A[e] * s[a] * B[int64_t(a) * F + f];
   }
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-// T[x; x'] = sum_s e^{h s} prod_mu W[s, x_mu] W[s, x'_mu]  with W the symmetric square
-// root of the Ising bond matrix (rows: spin +1, -1)
 __global__ void ising_tensor_kernel(double beta, double h, int d, double* T) {
   const int n = 1 << (2 * d);
   double c = sqrt(2.0 * cosh(beta)), sn = sqrt(2.0 * sinh(beta));
@@ -456,12 +504,27 @@ void copy_modes(double* dst, const double* src, const ModeIdx& m, double alpha, 
   TATRG_CUDA(cudaGetLastError());
 }
 
-void weighted_colsum(const double* X, int64_t F, int n, double* v, cudaStream_t s) {
-  fill(v, n, 0.0, s);
-  if (F * n == 0) return;
-  check_extent(X, F * n - 1, sizeof(double), "weighted_colsum");
-  weighted_colsum_kernel<<<grid_for(F * n), 256, n * sizeof(double), s>>>(X, F, n, v);
+namespace {
+// rows per block for the row-chunked reductions: about 4 blocks per SM
+int64_t row_chunk(int64_t F) { return std::max<int64_t>(64, cdiv(F, 4 * 152)); }
+
+void finish_partials(const double* part, int nb, int width, double* out, cudaStream_t s) {
+  finish_partials_kernel<<<int(cdiv(width, 256)), 256, 0, s>>>(part, nb, width, out);
   TATRG_CUDA(cudaGetLastError());
+}
+}  // namespace
+
+void weighted_colsum(const double* X, int64_t F, int n, double* v, cudaStream_t s) {
+  if (n == 0) return;
+  if (F == 0) { fill(v, n, 0.0, s); return; }
+  check_extent(X, F * n - 1, sizeof(double), "weighted_colsum");
+  check_extent(v, n - 1, sizeof(double), "weighted_colsum output");
+  const int64_t rows = row_chunk(F);
+  const int nb = int(cdiv(F, rows));
+  DevBuf part(size_t(nb) * n * sizeof(double), s);
+  weighted_colsum_kernel<<<nb, std::min(256, 32 * int(cdiv(n, 32))), 0, s>>>(X, F, n, rows, part.d());
+  TATRG_CUDA(cudaGetLastError());
+  finish_partials(part.d(), nb, n, v, s);
 }
 
 void flip_by_sign(double* X, int64_t F, int n, double* Y, int64_t G, const double* v,
@@ -476,27 +539,38 @@ void flip_by_sign(double* X, int64_t F, int n, double* Y, int64_t G, const doubl
 
 void trace_asb(const double* A, const double* sv, const double* B, int64_t F, int Da,
                double* out, cudaStream_t s) {
-  fill(out, 1, 0.0, s);
+  if (F * Da == 0) { fill(out, 1, 0.0, s); return; }
   check_extent(A, F * Da - 1, sizeof(double), "trace A");
   check_extent(B, F * Da - 1, sizeof(double), "trace B");
-  trace_kernel<<<grid_for(F * Da), 256, 0, s>>>(A, sv, B, F, Da, out);
+  const int nb = grid_for(F * Da);
+  DevBuf part(size_t(nb) * sizeof(double), s);
+  trace_kernel<<<nb, 256, 0, s>>>(A, sv, B, F, Da, part.d());
   TATRG_CUDA(cudaGetLastError());
+  finish_partials(part.d(), nb, 1, out, s);
 }
 
 void multiplet_overlap(const double* X, int64_t F, int n, int a, int m, double* G, cudaStream_t s) {
   TATRG_CHECK(m >= 1 && m <= 32 && a >= 0 && a + m <= n, TATRG_EINVAL, "multiplet_overlap: bad block");
   check_extent(X, F * n - 1, sizeof(double), "multiplet_overlap");
   check_extent(G, int64_t(m) * m - 1, sizeof(double), "multiplet_overlap G");
-  fill(G, int64_t(m) * m, 0.0, s);
-  multiplet_overlap_kernel<<<int(std::min<int64_t>(cdiv(F, 256), 608)), 256, 0, s>>>(X, F, n, a, m, G);
+  if (F == 0) { fill(G, int64_t(m) * m, 0.0, s); return; }
+  const int64_t rows = row_chunk(F);
+  const int nb = int(cdiv(F, rows));
+  DevBuf part(size_t(nb) * m * m * sizeof(double), s);
+  multiplet_overlap_kernel<<<nb, std::min(1024, 32 * int(cdiv(m * m, 32))), 0, s>>>(X, F, n, a, m, rows,
+                                                                                  part.d());
   TATRG_CUDA(cudaGetLastError());
+  finish_partials(part.d(), nb, m * m, G, s);
 }
 
 void sum_all(const double* x, int64_t n, double* out, cudaStream_t s) {
-  fill(out, 1, 0.0, s);
-  if (n == 0) return;
-  sum_kernel<<<grid_for(n), 256, 0, s>>>(x, n, out);
+  if (n == 0) { fill(out, 1, 0.0, s); return; }
+  check_extent(x, n - 1, sizeof(double), "sum_all");
+  const int nb = grid_for(n);
+  DevBuf part(size_t(nb) * sizeof(double), s);
+  sum_kernel<<<nb, 256, 0, s>>>(x, n, part.d());
   TATRG_CUDA(cudaGetLastError());
+  finish_partials(part.d(), nb, 1, out, s);
 }
 
 void ising_tensor(double beta, double h, int d, double* T, cudaStream_t s) {

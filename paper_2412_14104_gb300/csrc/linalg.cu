@@ -2,11 +2,9 @@
 // CholeskyQR2), inverse of the triangular factor, and the one-sided (Hestenes) Jacobi SVD
 // used for every core SVD / PSD eigenproblem of the RG step (swap core, triad Gram
 // eigenvectors, squeezer factors and core, re-split).
-#include <cooperative_groups.h>
 
 #include "kernels.cuh"
 
-namespace cg = cooperative_groups;
 
 namespace tatrg {
 namespace {
@@ -90,19 +88,24 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* Acg, int64_t m, in
                                                       int max_sweeps, double tol, int* status) {
   extern __shared__ double Ac[];
   __shared__ int rotated;
-  __shared__ double fro2;
+  __shared__ double fro2, wsum[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int64_t e = threadIdx.x; e < m * N; e += blockDim.x) Ac[e] = Acg[e];
   // Columns whose squared norm is below (4 eps)^2 ||A||_F^2 sit at the rounding floor:
   // they are treated as converged, otherwise rounding in a large-small pair keeps the
   // relative inner product above tol forever.
-  if (threadIdx.x == 0) fro2 = 0.0;
   __syncthreads();
   {
     double acc = 0.0;
     for (int64_t e = threadIdx.x; e < m * N; e += blockDim.x) acc = fma(Ac[e], Ac[e], acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) atomicAdd(&fro2, acc);
+    if (lane == 0) wsum[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += wsum[w];
+      fro2 = t;
+    }
   }
   __syncthreads();
   const double floor2 = 7.9e-31 * fro2;
@@ -290,14 +293,52 @@ __global__ void __launch_bounds__(256) tall_jacobi_round_kernel(double* Ac, int6
   }
 }
 
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier over co-resident blocks with a time limit.  bar[0] counts arrivals,
+// bar[1] is the generation, bar[2] the abort flag.  Thread 0 of each block reads the
+// generation, arrives, and the last block to arrive resets the count and advances the
+// generation; the others wait for that, at most 2 s, after which they set the abort flag.
+// Every block returns false once the abort flag is set, so no block waits for ever.
+__device__ bool grid_barrier(unsigned* bar) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vb = bar;
+    const unsigned gen = vb[1];
+    __threadfence();
+    if (atomicAdd(&bar[0], 1u) + 1u == gridDim.x) {
+      atomicExch(&bar[0], 0u);
+      __threadfence();
+      atomicAdd(&bar[1], 1u);
+      ok = 1;
+    } else {
+      const uint64_t t0 = global_ns();
+      while (vb[1] == gen && vb[2] == 0u) {
+        if (global_ns() - t0 > 2000000000ull) { atomicExch(&bar[2], 1u); break; }
+        __nanosleep(64);
+      }
+      ok = vb[1] != gen;
+    }
+    __threadfence();
+    if (vb[2] != 0u) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 // The same rotations as tall_jacobi_round_kernel, all sweeps in one cooperative launch:
 // block b handles pairs b, b + gridDim.x, ... of each round and a grid-wide barrier
 // separates rounds.  All blocks decide convergence from the same flag after a barrier.
+// status: 0 converged, 1 not converged within max_sweeps, 2 a barrier timed out.
 __global__ void __launch_bounds__(256) coop_jacobi_kernel(double* Ac, int64_t m, int N, double* Vc,
                                                           double tol, const double* fro2,
                                                           int* rotated, int* status,
-                                                          int max_sweeps) {
-  cg::grid_group grid = cg::this_grid();
+                                                          int max_sweeps, unsigned* bar) {
   __shared__ double red[3][8];
   __shared__ double cs[2];
   __shared__ int doit;
@@ -357,15 +398,20 @@ __global__ void __launch_bounds__(256) coop_jacobi_kernel(double* Ac, int64_t m,
         }
         __syncthreads();
       }
-      grid.sync();
+      if (!grid_barrier(bar)) goto timed_out;
     }
-    const int any = atomicAdd(rotated, 0);
-    grid.sync();  // every block has read the flag
-    if (blockIdx.x == 0 && threadIdx.x == 0) *rotated = 0;
-    grid.sync();
-    if (!any) { converged = 1; break; }
+    {
+      const int any = atomicAdd(rotated, 0);
+      if (!grid_barrier(bar)) goto timed_out;  // every block has read the flag
+      if (blockIdx.x == 0 && threadIdx.x == 0) *rotated = 0;
+      if (!grid_barrier(bar)) goto timed_out;
+      if (!any) { converged = 1; break; }
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *status = converged ? 0 : 1;
+  return;
+timed_out:
+  if (threadIdx.x == 0) atomicExch(status, 2);
 }
 
 __global__ void sumsq_kernel(const double* x, int64_t n, double* out) {
@@ -384,11 +430,9 @@ void cholesky(const double* G, int n, double* R, int* status_dev, double shift_r
   check_extent(R, int64_t(n) * n - 1, sizeof(double), "cholesky output");
   TATRG_CHECK(n >= 1 && n <= 160, TATRG_EINVAL, "cholesky: n must be <= 160");
   const size_t sm = size_t(n) * (n + 1) / 2 * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
-    TATRG_CUDA(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 161 / 2 * 8));
-    attr = true;
-  }
+  static const cudaError_t attr = cudaFuncSetAttribute(  // once, thread-safe
+      cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 161 / 2 * 8);
+  TATRG_CUDA(attr);
   cholesky_kernel<<<1, 1024, sm, s>>>(G, n, R, status_dev, shift_rel);
   TATRG_CUDA(cudaGetLastError());
 }
@@ -417,37 +461,36 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
   const double tol = std::max(1e-15, 2.220446049250313e-16 * std::sqrt(double(m)));
   if ((m * N * 8 <= 200 * 1024 && N < 32) || N < 4) {
     int threads = 32 * std::max(1, std::min(32, N / 2));
-    static bool attr = false;
-    if (!attr) {
-      TATRG_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-      attr = true;
-    }
+    static const cudaError_t attr = cudaFuncSetAttribute(  // once, thread-safe
+        jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    TATRG_CUDA(attr);
     jacobi_kernel<<<1, threads, size_t(m * N) * sizeof(double), s>>>(ac.d(), m, N, vc.d(), 60, tol, status_dev);
     TATRG_CUDA(cudaGetLastError());
   } else {
     // tall: one block per pair and one launch per round; the host reads the rotation flag
     // once per sweep.
-    DevBuf aux(2 * sizeof(double), s);
+    DevBuf aux(4 * sizeof(double), s);
     double* fro2 = aux.d();
     int* rot = reinterpret_cast<int*>(aux.d() + 1);
-    TATRG_CUDA(cudaMemsetAsync(fro2, 0, sizeof(double), s));
+    unsigned* bar = reinterpret_cast<unsigned*>(aux.d() + 2);
+    TATRG_CUDA(cudaMemsetAsync(aux.d(), 0, 4 * sizeof(double), s));
     sumsq_kernel<<<int(std::min<int64_t>(cdiv(m * N, 256), 1024)), 256, 0, s>>>(ac.d(), m * N, fro2);
     TATRG_CUDA(cudaGetLastError());
-    // all sweeps in one cooperative launch (the blocks are co-resident by construction)
+    // all sweeps in one cooperative launch (its blocks are co-resident by construction; the
+    // barrier between rounds still gives up after 2 s and reports status 2)
     int thr = m >= 256 ? 256 : (m >= 128 ? 128 : 64);
     int dev = 0, sms = 0, per_sm = 0;
     TATRG_CUDA(cudaGetDevice(&dev));
     TATRG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     TATRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_jacobi_kernel, thr, 0));
     const int blocks = std::max(1, std::min(N / 2, per_sm * sms));
-    TATRG_CUDA(cudaMemsetAsync(rot, 0, sizeof(int), s));
     int max_sweeps = 60;
     double tol_ = tol;
     double* acp = ac.d();
     double* vcp = vc.d();
     int64_t m_ = m;
     int N_ = N;
-    void* args[] = {&acp, &m_, &N_, &vcp, &tol_, &fro2, &rot, &status_dev, &max_sweeps};
+    void* args[] = {&acp, &m_, &N_, &vcp, &tol_, &fro2, &rot, &status_dev, &max_sweeps, &bar};
     TATRG_CUDA(cudaLaunchCooperativeKernel((void*)coop_jacobi_kernel, dim3(blocks), dim3(thr), args, 0, s));
     if (st) st->launches += 1;
   }

@@ -4,7 +4,9 @@
 // and tensors (Eqs. 2-4), squeezers (Eq. 5), contraction (Eqs. 6-7), re-split.
 #include <cmath>
 #include <cstring>
+#include <atomic>
 #include <mutex>
+#include <thread>
 #include <string>
 
 #include "engine.cuh"
@@ -965,16 +967,54 @@ tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double 
                          int nsteps, double* lnZ_out) {
   if (!ctx || !betas || !lnZ_out || nbeta < 0) return TATRG_EINVAL;
   return guard(ctx, [&] {
-    for (int i = 0; i < nbeta; ++i) {
-      tatrg_params pp = ctx->p;
-      tatrg_ctx sub(pp, ctx->stream);
-      sub.replica = uint32_t(i);
-      sub.init_ising(betas[i], h, d);
-      for (int k = 0; k < nsteps; ++k) sub.rg_step();
-      double tt = sub.trace();
-      TATRG_CHECK(tt > 0.0, TATRG_ENUMERIC, "non-positive final trace in sweep");
-      lnZ_out[i] = sub.partial_lnz() + std::ldexp(std::log(tt), -sub.step);
+    TATRG_CHECK(d >= 2 && d <= 4 && nsteps >= 0, TATRG_EINVAL, "tatrg_sweep: bad d or step count");
+    // The temperatures are independent runs.  Worker threads take them in turn, each
+    // with its own non-blocking stream and context, so the many small kernels and host
+    // decisions of one run overlap with the large contractions of the others.  Run i uses
+    // sketch replica i, so the results do not depend on the scheduling.
+    const int nw = std::max(1, std::min(nbeta, ctx->p.sweep_workers > 0 ? ctx->p.sweep_workers : 8));
+    int dev = 0;
+    TATRG_CUDA(cudaGetDevice(&dev));
+    tc_available();  // one-time initialisation before the workers start
+    TATRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::atomic<int> next(0);
+    std::mutex mu;
+    tatrg_status first = TATRG_OK;
+    std::string first_msg;
+    auto fail = [&](tatrg_status c, const std::string& m) {
+      std::lock_guard<std::mutex> l(mu);
+      if (first == TATRG_OK) { first = c; first_msg = m; }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 0; w < nw; ++w) {
+      pool.emplace_back([&]() {
+        cudaStream_t s = nullptr;
+        try {
+          TATRG_CUDA(cudaSetDevice(dev));
+          TATRG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+          for (int i = next++; i < nbeta && first == TATRG_OK; i = next++) {
+            tatrg_ctx sub(ctx->p, s);
+            sub.replica = uint32_t(i);
+            sub.init_ising(betas[i], h, d);
+            for (int k = 0; k < nsteps; ++k) sub.rg_step();
+            double tt = sub.trace();
+            TATRG_CHECK(tt > 0.0 && std::isfinite(tt), TATRG_ENUMERIC, "non-positive final trace in sweep");
+            lnZ_out[i] = sub.partial_lnz() + std::ldexp(std::log(tt), -sub.step);
+          }
+        } catch (const Error& e) {
+          fail(e.code, e.what());
+        } catch (const std::exception& e) {
+          fail(TATRG_ECUDA, e.what());
+        }
+        if (s) {
+          cudaStreamSynchronize(s);
+          cudaStreamDestroy(s);
+        }
+      });
     }
+    for (auto& t : pool) t.join();
+    TATRG_CHECK(tc_error_flag(true) == 0, TATRG_ETIMEOUT, "a tensor-core pipeline wait timed out");
+    if (first != TATRG_OK) throw Error(first, first_msg);
   });
 }
 

@@ -413,17 +413,15 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {  // once, thread-safe
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
+      return reinterpret_cast<EncodeTiledFn>(p);
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -449,11 +447,9 @@ void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& b
   constexpr int KC = PREC == 1 ? TATRG_KC_TF32 : TATRG_KC_BF16;  // stages per FP32 chain
   constexpr int SMEM = STAGES * STAGE + 1024;
   auto k = tc_gemm_kernel<PREC, KC, STAGES>;
-  static bool attr = false;
-  if (!attr) {
-    TATRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-    attr = true;
-  }
+  static const cudaError_t attr =  // once per instantiation, thread-safe
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  TATRG_CUDA(attr);
   k<<<grid, 320, SMEM, s>>>(ahi, alo, bhi, blo, a);
   TATRG_CUDA(cudaGetLastError());
 }
@@ -461,16 +457,14 @@ void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& b
 }  // namespace
 
 bool tc_available() {
-  static int ok = -1;
-  if (ok < 0) {
+  static const bool ok = []() {  // once, thread-safe
     int dev = 0, major = 0, minor = 0;
-    ok = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess)
-      ok = (major == 10 && minor == 3 && encode_fn() != nullptr) ? 1 : 0;
-  }
-  return ok == 1;
+    return cudaGetDevice(&dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess &&
+           major == 10 && minor == 3 && encode_fn() != nullptr;
+  }();
+  return ok;
 }
 
 int tc_error_flag(bool reset) {

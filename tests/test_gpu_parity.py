@@ -145,3 +145,27 @@ def test_errors_are_reported():
         ctx.init_ising(-1.0, 0.0, 4)
     with pytest.raises(tg.TatrgError):
         ctx.init_ising(0.1, 0.0, 5)
+
+
+def test_temperature_sweep_matches_single_runs():
+    """β-sweep: temperature i runs with sketch replica i, so each result equals the oracle's
+    single run with that replica, whatever the number of concurrent workers."""
+    betas = [0.12, 0.1497, 0.2, 0.3, 0.05]
+    want = [trg.lnz_per_site(b, 1e-4, 4, trg.Params(8, 2, q=2, seed=3, replica=i), 10)
+            for i, b in enumerate(betas)]
+    runs = [tg.Context(8, 2, 2, seed=3, sweep_workers=w).sweep(betas, 1e-4, 4, 10) for w in (1, 3)]
+    for i in range(len(betas)):
+        assert abs(runs[0][i] - want[i]) < 1e-11 * abs(want[i]), i
+    assert np.array_equal(runs[0], runs[1])
+
+
+def test_fp64_runs_are_reproducible():
+    """Every FP64 reduction adds in a fixed order, so a repeated run gives the same bits."""
+    out = []
+    for _ in range(2):
+        ctx = tg.Context(10, 2, 2, seed=5).init_ising(0.1497, 1e-4, 4).rg_step(6)
+        out.append((ctx.get_state(), ctx.lnZ()))
+    (A0, s0, B0), z0 = out[0]
+    (A1, s1, B1), z1 = out[1]
+    assert z0 == z1
+    assert np.array_equal(A0, A1) and np.array_equal(s0, s1) and np.array_equal(B0, B1)
