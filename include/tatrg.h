@@ -92,9 +92,21 @@ tatrg_status tatrg_rg_step(tatrg_ctx* ctx, int nsteps);
  * Writes one double to a host pointer.  Synchronises. */
 tatrg_status tatrg_lnZ(tatrg_ctx* ctx, double* lnZ_per_site);
 
-/* Derivatives of ln Z / V with respect to beta and h (internal energy, magnetisation,
- * and optionally the second beta derivative for the specific heat).  Not built in this
- * version: returns TATRG_ENOTIMPL. */
+/* Derivatives of the computed ln Z / V (tatrg_lnZ after the same steps) with respect to
+ * beta and h: -dlnZ_dbeta is the internal energy per site (the beta derivative of beta f,
+ * with the free energy f = -ln Z / (beta V) of Sec. 3), dlnZ_dh the magnetisation per site,
+ * d2lnZ_dbeta2 the specific heat over beta^2.  The paper computes ln Z only; these are the
+ * exact derivatives of the algorithm's output as a function of (beta, h), with every
+ * sketch held fixed, obtained by forward-mode (tangent) propagation through all steps of
+ * the run: one FP64 pass per first derivative (whatever the context's precision), and
+ * the second derivative as the central difference (step 1e-6 max(1, beta)) of the exact
+ * first derivative (two more passes).  The computed ln Z / V is piecewise smooth: where
+ * kept singular values of different symmetry sectors cross, the ordered basis that later
+ * sketches act on changes and ln Z / V jumps at the level of the truncation error; the
+ * derivatives are those of the piece that contains (beta, h).  Needs a state made by tatrg_init_ising; any of the
+ * three host pointers may be null (not all).  Runs on the context's stream, synchronises,
+ * and leaves the context's state untouched.  At h = 0 the h-derivative of the algorithm
+ * is not smooth where symmetry-degenerate values split; use it at h != 0. */
 tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh,
                         double* d2lnZ_dbeta2 /* nullable */);
 

@@ -12,6 +12,7 @@ Layout
 ``ising``   the 4D (or 2D/3D) Ising initial tensor T of Sec. 3 and its first split.
 ``trg``     one coarse-graining step (bond swap Eq. 1, triad Eqs. 2-4, squeezers Eq. 5,
             contraction Eqs. 6-7, re-split) and the ln Z accumulation.
+``derivatives``  dlnZ/dbeta and dlnZ/dh of the computed ln Z / V (central differences).
 
 Everything is float64 NumPy; contractions are written as ``numpy.einsum`` with the index
 names of the paper so that each one can be checked against its equation by eye.

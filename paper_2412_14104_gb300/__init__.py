@@ -140,10 +140,12 @@ class Context:
         _check(lib().tatrg_lnZ(self._h, ctypes.byref(out)), self._h)
         return out.value
 
-    def grad(self):
+    def grad(self, second=False):
+        """(dlnZ/dbeta, dlnZ/dh, d2lnZ/dbeta2 or None) of the run so far, per site."""
         a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        _check(lib().tatrg_grad(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), self._h)
-        return a.value, b.value, c.value
+        _check(lib().tatrg_grad(self._h, ctypes.byref(a), ctypes.byref(b),
+                                ctypes.byref(c) if second else None), self._h)
+        return a.value, b.value, (c.value if second else None)
 
     def sweep(self, betas, h, d, nsteps):
         b = np.ascontiguousarray(betas, dtype=np.float64)
@@ -237,3 +239,29 @@ def svd_noalloc(A, U, S, V, stream=None):
     _check(lib().tatrg_svd_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(U.data_ptr()),
                                    ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
                                    _stream_ptr(stream)))
+
+
+def lnz_function(chi, r, q=2, method=TRIAD, precision=FP64, seed=0, d=4, nsteps=8):
+    """ln Z / V of a run as a torch.autograd.Function of the scalar tensors (beta, h).
+
+    The forward call runs the RG steps and the tangent passes of tatrg_grad; backward
+    returns grad_output times dlnZ/dbeta and dlnZ/dh.  Both inputs are 0-d float64 tensors.
+    """
+    import torch
+
+    class _LnZ(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, beta, h):
+            ctx = Context(chi, r, q, method=method, precision=precision, seed=seed)
+            ctx.init_ising(float(beta), float(h), d).rg_step(nsteps)
+            lnz = ctx.lnZ()
+            gb, gh, _ = ctx.grad()
+            fctx.save_for_backward(torch.tensor([gb, gh], dtype=torch.float64))
+            return torch.tensor(lnz, dtype=torch.float64)
+
+        @staticmethod
+        def backward(fctx, grad_out):
+            (g,) = fctx.saved_tensors
+            return grad_out * g[0], grad_out * g[1]
+
+    return _LnZ.apply

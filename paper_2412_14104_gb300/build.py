@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libtatrg.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["kernels_f64.cu", "linalg.cu", "engine.cu", "tc_gemm.cu", "tatrg.cu"]
+SOURCES = ["kernels_f64.cu", "linalg.cu", "engine.cu", "tangent.cu", "tc_gemm.cu", "tatrg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -70,6 +70,32 @@ class Engine {
   };
   MetricOrth orth_metric(const double* X, int64_t nin, int64_t w, const Op& metric);
 
+  // Forward-mode (tangent) rules, in tangent.cu.  grp[i] is the multiplet id of singular
+  // value i: pairs inside one multiplet get no mutual rotation.
+  struct SvdTan {
+    DMat U, V;              // tangents of the leading kt columns of U (m x kt) and V (n x kt)
+    std::vector<double> s;  // tangents of the leading kt singular values
+  };
+  SvdTan svd_tan(const double* Ad, int64_t m, int64_t n, const SvdResult& e, int kt,
+                 const std::vector<int>& grp);
+  struct OrthT {
+    OrthResult o;
+    DMat Qd, Rd;
+  };
+  // FP64 orth (CholeskyQR2, rank-revealing SVD fallback) with the tangents of Q and R
+  OrthT orth_t(const double* Y, const double* Yd, int64_t m, int64_t n, double tau);
+  struct RsvdT {
+    SvdResult e;
+    SvdTan t;
+  };
+  // rsvd / rsvd_psd with tangents; apply_d and rapply_d apply dM and dM^T
+  RsvdT rsvd_t(const Op& apply, const Op& rapply, const Op& apply_d, const Op& rapply_d,
+               int64_t rows, int64_t cols, int64_t ell, int q, const double* omega, double tau);
+  RsvdT rsvd_psd_t(const double* rho, const double* rho_d, int64_t n, int64_t ell, int q,
+                   const double* omega, double tau);
+  DevBuf polar_tan(const SvdResult& e, const double* Gd, int m);
+  DevBuf upload(const std::vector<double>& v);
+
   std::vector<double> to_host(const double* p, int64_t n);
   int read_flag(int idx = 0);
   int* flag(int idx = 0) { return flag_.as<int>() + idx; }
@@ -83,5 +109,12 @@ class Engine {
 };
 
 int keep_count(const std::vector<double>& v, double rel, int64_t cap);
+// multiplet id of each value of a descending sequence (gap <= tau times the larger value)
+std::vector<int> multiplet_groups(const std::vector<double>& v, double tau);
+// tangent.cu: y += a x;  x *= v^p with dx <- dx v^p + p x v^(p-1) dv;  dT/dtheta of Ising T
+void axpy(double* y, const double* x, int64_t n, double a, cudaStream_t s);
+void scale_axis_tan(double* x, double* dx, const double* v, const double* dv, int64_t outer,
+                    int64_t n, int64_t inner, int power, cudaStream_t s);
+void ising_tensor_tan(double beta, double h, int d, int dir, double* dT, cudaStream_t s);
 
 }  // namespace tatrg

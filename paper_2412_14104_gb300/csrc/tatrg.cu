@@ -90,6 +90,14 @@ struct tatrg_ctx {
   std::vector<double> spec_s, spec_sigma;
   std::vector<std::vector<double>> spec_sq;
   double flops[ST_N] = {0, 0, 0, 0, 0};
+  // Forward-mode tangent along one input (tan_dir 0: beta, 1: h), carried beside the
+  // state when tan_on: dA, dB, ds and d ln c_k.  Tangent runs are FP64 throughout.
+  bool tan_on = false;
+  int tan_dir = 0;
+  DevBuf Ad, Bd, sdd;
+  std::vector<double> sd, lnc_d;
+  double beta0 = 0.0, h0 = 0.0;  // parameters of the last init_ising
+  bool ising = false;            // the state comes from init_ising (not set_state)
 
   tatrg_ctx(const tatrg_params& pp, cudaStream_t s) : p(pp), stream(s), eng(s) {
     eng.stats().timing = pp.profile != 0;
@@ -113,43 +121,55 @@ struct tatrg_ctx {
   void upload_s() {
     sdev = DevBuf(std::max<int64_t>(Da, 1) * sizeof(double), stream);
     TATRG_CUDA(cudaMemcpyAsync(sdev.d(), s.data(), Da * sizeof(double), cudaMemcpyHostToDevice, stream));
+    if (tan_on) sdd = eng.upload(sd);
   }
+  DevBuf tbuf(int64_t n) { return tan_on ? dalloc(n, stream) : DevBuf(); }
 
   // Apply the sign convention to the columns of X (F x n, row-major): v = w^T X with the
-  // hashed weights; flip the columns (and those of Y, F2 x n, if given) where v < 0.
-  void fix_sign_cols(double* X, int64_t F, int n, double* Y, int64_t F2) {
+  // hashed weights; flip the columns (and those of Y, F2 x n, if given) where v < 0.  The
+  // tangents Xd, Yd (may be null) flip with them.
+  void fix_sign_cols(double* X, int64_t F, int n, double* Y, int64_t F2, double* Xd = nullptr,
+                     double* Yd = nullptr) {
     DevBuf v(std::max(n, 1) * sizeof(double), stream);
     weighted_colsum(X, F, n, v.d(), stream);
     flip_by_sign(X, F, n, nullptr, 0, v.d(), stream);
     if (Y) flip_by_sign(Y, F2, n, nullptr, 0, v.d(), stream);
+    if (Xd) flip_by_sign(Xd, F, n, nullptr, 0, v.d(), stream);
+    if (Yd) flip_by_sign(Yd, F2, n, nullptr, 0, v.d(), stream);
   }
   // Same, but Y is n x F2 (flip its rows).
-  void fix_sign_cols_rows(double* X, int64_t F, int n, double* Y, int64_t F2) {
+  void fix_sign_cols_rows(double* X, int64_t F, int n, double* Y, int64_t F2, double* Xd = nullptr,
+                          double* Yd = nullptr) {
     DevBuf v(std::max(n, 1) * sizeof(double), stream);
     weighted_colsum(X, F, n, v.d(), stream);
     flip_by_sign(X, F, n, Y, F2, v.d(), stream);
+    if (Xd) flip_by_sign(Xd, F, n, Yd, Yd ? F2 : 0, v.d(), stream);
   }
 
   // Canonical basis of the columns of X (F x n): the sign rule for single columns and, for
   // each degenerate multiplet of vals, the rotation V_M -> V_M O with O the polar factor
   // of V_M^T W (W: hashed weights).  The same rotation is applied to Y: to its rows when
-  // y_rows (Y is n x F2), else to its columns (Y is F2 x n).
+  // y_rows (Y is n x F2), else to its columns (Y is F2 x n).  Xd, Yd: tangents (may be null).
   void canonical_cols(double* X, int64_t F, int n, const std::vector<double>& vals, double* Y,
-                      int64_t F2, bool y_rows);
+                      int64_t F2, bool y_rows, double* Xd = nullptr, double* Yd = nullptr);
   void init_ising(double beta, double h, int dd);
   void rg_step();
   void resplit_and_rotate(DMat& phi, DMat& psi, int64_t rows, int64_t Dg,
-                          const std::vector<int64_t>& newD);
+                          const std::vector<int64_t>& newD, DMat* phid = nullptr,
+                          DMat* psid = nullptr);
   double trace();
-  DMat isometry(const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out);
-  void factor(const double* rho, int64_t P, int kind, DMat& Rt);
+  double trace_tan(double tt);  // d ln tTr given tTr
+  DMat isometry(const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out,
+                const double* rhod = nullptr, DMat* Ud = nullptr);
+  void factor(const double* rho, int64_t P, int kind, DMat& Rt, const double* rhod = nullptr,
+              DMat* Rtd = nullptr);
 };
 
 // ---------------------------------------------------------------------------------
 void tatrg_ctx::canonical_cols(double* X, int64_t F, int n, const std::vector<double>& vals,
-                               double* Y, int64_t F2, bool y_rows) {
-  if (y_rows) fix_sign_cols_rows(X, F, n, Y, F2);
-  else fix_sign_cols(X, F, n, Y, F2);
+                               double* Y, int64_t F2, bool y_rows, double* Xd, double* Yd) {
+  if (y_rows) fix_sign_cols_rows(X, F, n, Y, F2, Xd, Yd);
+  else fix_sign_cols(X, F, n, Y, F2, Xd, Yd);
   const int saved = eng.prec;
   eng.prec = 0;
   for (auto& ab : multiplets(vals, n, tau)) {
@@ -159,18 +179,53 @@ void tatrg_ctx::canonical_cols(double* X, int64_t F, int n, const std::vector<do
     multiplet_overlap(X, F, n, a, m, G.d(), stream);
     SvdResult e = eng.svd(G.d(), m, m);
     eng.mm(m, m, m, e.U.p(), m, false, e.V.p(), m, true, O.d(), m);  // O = U V^T
+    DevBuf Od;
+    if (Xd) {  // dO from dG = dX_M^T W (the overlap is linear in X)
+      DevBuf Gd(m * m * sizeof(double), stream);
+      multiplet_overlap(Xd, F, n, a, m, Gd.d(), stream);
+      Od = eng.polar_tan(e, Gd.d(), m);
+    }
+    // X[:, a:a+m] <- X[:, a:a+m] O   (dX_M <- dX_M O + X_M dO, from the old X_M)
+    const GemmDesc gx = G_(modes({{F, n, m}}), modes({{m, 1, 1}}), modes({{m, 1, m}}));
+    const ModeIdx back = modes({{F, m, n}, {m, 1, 1}});
     DevBuf T(F * m * sizeof(double), stream);
-    // X[:, a:a+m] <- X[:, a:a+m] O
-    eng.gemm(G_(modes({{F, n, m}}), modes({{m, 1, 1}}), modes({{m, 1, m}})), X + a, O.d(), T.d());
-    copy_modes(X + a, T.d(), modes({{F, m, n}, {m, 1, 1}}), 1.0, stream);
+    eng.gemm(gx, X + a, O.d(), T.d());
+    if (Xd) {
+      DevBuf Td(F * m * sizeof(double), stream);
+      eng.gemm(gx, Xd + a, O.d(), Td.d());
+      GemmDesc g1 = gx;
+      g1.beta = 1.0;
+      eng.gemm(g1, X + a, Od.d(), Td.d());
+      copy_modes(Xd + a, Td.d(), back, 1.0, stream);
+    }
+    copy_modes(X + a, T.d(), back, 1.0, stream);
     if (Y) {
       DevBuf T2(F2 * m * sizeof(double), stream);
       if (y_rows) {  // Y[a:a+m, :] <- O^T Y[a:a+m, :]
-        eng.gemm(G_(modes({{m, 1, F2}}), modes({{F2, 1, 1}}), modes({{m, m, F2}})), O.d(), Y + a * F2, T2.d());
+        const GemmDesc gy = G_(modes({{m, 1, F2}}), modes({{F2, 1, 1}}), modes({{m, m, F2}}));
+        eng.gemm(gy, O.d(), Y + a * F2, T2.d());
+        if (Yd) {
+          DevBuf T2d(F2 * m * sizeof(double), stream);
+          eng.gemm(gy, O.d(), Yd + a * F2, T2d.d());
+          GemmDesc g1 = gy;
+          g1.beta = 1.0;
+          eng.gemm(g1, Od.d(), Y + a * F2, T2d.d());
+          copy_modes(Yd + a * F2, T2d.d(), modes({{m * F2, 1, 1}}), 1.0, stream);
+        }
         copy_modes(Y + a * F2, T2.d(), modes({{m * F2, 1, 1}}), 1.0, stream);
       } else {       // Y[:, a:a+m] <- Y[:, a:a+m] O
-        eng.gemm(G_(modes({{F2, n, m}}), modes({{m, 1, 1}}), modes({{m, 1, m}})), Y + a, O.d(), T2.d());
-        copy_modes(Y + a, T2.d(), modes({{F2, m, n}, {m, 1, 1}}), 1.0, stream);
+        const GemmDesc gy = G_(modes({{F2, n, m}}), modes({{m, 1, 1}}), modes({{m, 1, m}}));
+        const ModeIdx backy = modes({{F2, m, n}, {m, 1, 1}});
+        eng.gemm(gy, Y + a, O.d(), T2.d());
+        if (Yd) {
+          DevBuf T2d(F2 * m * sizeof(double), stream);
+          eng.gemm(gy, Yd + a, O.d(), T2d.d());
+          GemmDesc g1 = gy;
+          g1.beta = 1.0;
+          eng.gemm(g1, Y + a, Od.d(), T2d.d());
+          copy_modes(Yd + a, T2d.d(), backy, 1.0, stream);
+        }
+        copy_modes(Y + a, T2.d(), backy, 1.0, stream);
       }
     }
   }
@@ -179,6 +234,8 @@ void tatrg_ctx::canonical_cols(double* X, int64_t F, int n, const std::vector<do
 
 void tatrg_ctx::init_ising(double beta, double h, int dd) {
   d = dd;
+  beta0 = beta;
+  h0 = h;
   const int64_t n = int64_t(1) << d;
   eng.prec = 0;
   DevBuf T(n * n * sizeof(double), stream);
@@ -194,13 +251,34 @@ void tatrg_ctx::init_ising(double beta, double h, int dd) {
   B = DevBuf(n * Da * sizeof(double), stream);
   copy_modes(A.d(), e.U.p(), modes({{n, e.U.cols, Da}, {Da, 1, 1}}), 1.0, stream);
   copy_modes(B.d(), e.V.p(), modes({{Da, 1, n}, {n, e.V.cols, 1}}), 1.0, stream);
-  fix_sign_cols_rows(A.d(), n, int(Da), B.d(), n);
+  std::vector<double> ds;
+  if (tan_on) {
+    DevBuf Td(n * n * sizeof(double), stream);
+    ising_tensor_tan(beta, h, d, tan_dir, Td.d(), stream);
+    Engine::SvdTan t = eng.svd_tan(Td.d(), n, n, e, int(Da), multiplet_groups(e.s, 1e-10));
+    Ad = DevBuf(n * Da * sizeof(double), stream);
+    Bd = DevBuf(n * Da * sizeof(double), stream);
+    copy_modes(Ad.d(), t.U.p(), modes({{n * Da, 1, 1}}), 1.0, stream);
+    copy_modes(Bd.d(), t.V.p(), modes({{Da, 1, n}, {n, Da, 1}}), 1.0, stream);
+    ds = t.s;
+  }
+  fix_sign_cols_rows(A.d(), n, int(Da), B.d(), n, tan_on ? Ad.d() : nullptr, tan_on ? Bd.d() : nullptr);
   s.assign(e.s.begin(), e.s.begin() + Da);
+  lnc.assign(1, std::log(c0));
+  if (tan_on) {
+    // c0 = ||s||, s' = s / c0:  dc0 = s . ds / c0,  ds' = ds / c0 - s dc0 / c0^2
+    double dc = 0.0;
+    for (int64_t i = 0; i < Da; ++i) dc += s[i] * ds[i];
+    dc /= c0;
+    sd.assign(Da, 0.0);
+    for (int64_t i = 0; i < Da; ++i) sd[i] = ds[i] / c0 - s[i] * dc / (c0 * c0);
+    lnc_d.assign(1, dc / c0);
+  }
   for (auto& x : s) x /= c0;
   upload_s();
-  lnc.assign(1, std::log(c0));
   step = 0;
   ready = true;
+  ising = true;
   TATRG_CUDA(cudaStreamSynchronize(stream));
 }
 
@@ -210,8 +288,21 @@ double tatrg_ctx::trace() {
   return eng.to_host(out.d(), 1)[0];
 }
 
+// d ln tTr = (tTr(dA, s, B) + tTr(A, ds, B) + tTr(A, s, dB)) / tTr
+double tatrg_ctx::trace_tan(double tt) {
+  const int64_t F = prod(D, 0, D.size());
+  DevBuf out(3 * sizeof(double), stream);
+  trace_asb(Ad.d(), sdev.d(), B.d(), F, int(Da), out.d(), stream);
+  trace_asb(A.d(), sdd.d(), B.d(), F, int(Da), out.d() + 1, stream);
+  trace_asb(A.d(), sdev.d(), Bd.d(), F, int(Da), out.d() + 2, stream);
+  std::vector<double> v = eng.to_host(out.d(), 3);
+  return (v[0] + v[1] + v[2]) / tt;
+}
+
 // Leading eigenvectors of a PSD Gram (Eqs. 2-3): exact (k >= G) or RSVD with ell = k.
-DMat tatrg_ctx::isometry(const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out) {
+// With rhod (tangent mode) also the tangent of U in *Ud (constant for ATRG).
+DMat tatrg_ctx::isometry(const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out,
+                         const double* rhod, DMat* Ud) {
   DMat U;
   if (p.method == TATRG_ATRG) {
     U.buf = dalloc(Gd * Gd, stream);
@@ -221,16 +312,29 @@ DMat tatrg_ctx::isometry(const double* rho, int64_t Gd, int kind, std::vector<do
     DevBuf one(sizeof(double), stream);
     fill(one.d(), 1, 1.0, stream);
     copy_modes(U.p(), one.d(), diag, 1.0, stream);
+    if (rhod && Ud) {
+      Ud->buf = dalloc(Gd * Gd, stream);
+      Ud->rows = Ud->cols = Gd;
+      fill(Ud->p(), Gd * Gd, 0.0, stream);
+    }
     return U;
   }
   const int64_t k = std::min(width(), Gd);
   SvdResult e;
+  Engine::SvdTan et;
   if (k >= Gd) {
     e = eng.svd(rho, Gd, Gd);
+    if (rhod) et = eng.svd_tan(rhod, Gd, Gd, e, keep_count(e.s, 1e-14, k), multiplet_groups(e.s, tau));
   } else {
     DevBuf om(Gd * k * sizeof(double), stream);
     gaussian(p.seed, stream_id(step, kind), replica, Gd * k, om.d(), stream);
-    e = eng.rsvd_psd(rho, Gd, k, p.q, om.d());
+    if (rhod) {
+      Engine::RsvdT r = eng.rsvd_psd_t(rho, rhod, Gd, k, p.q, om.d(), tau);
+      e = std::move(r.e);
+      et = std::move(r.t);
+    } else {
+      e = eng.rsvd_psd(rho, Gd, k, p.q, om.d());
+    }
   }
   int keep = keep_count(e.s, 1e-14, k);
   TATRG_CHECK(keep >= 1, TATRG_ENUMERIC, "triad Gram is zero");
@@ -238,21 +342,37 @@ DMat tatrg_ctx::isometry(const double* rho, int64_t Gd, int kind, std::vector<do
   U.rows = Gd;
   U.cols = keep;
   copy_modes(U.p(), e.U.p(), modes({{Gd, e.U.cols, keep}, {keep, 1, 1}}), 1.0, stream);
-  fix_sign_cols(U.p(), Gd, keep, nullptr, 0);
+  if (rhod) {
+    Ud->buf = dalloc(Gd * keep, stream);
+    Ud->rows = Gd;
+    Ud->cols = keep;
+    copy_modes(Ud->p(), et.U.p(), modes({{Gd, et.U.cols, keep}, {keep, 1, 1}}), 1.0, stream);
+  }
+  fix_sign_cols(U.p(), Gd, keep, nullptr, 0, rhod ? Ud->p() : nullptr);
   if (lam_out) *lam_out = e.s;
   return U;
 }
 
-// rho ~= R^T R from the leading eigenpairs (exact when ell >= P); returns R^T (P x keep).
-void tatrg_ctx::factor(const double* rho, int64_t P, int kind, DMat& Rt) {
+// rho ~= R^T R from the leading eigenpairs (exact when ell >= P); returns R^T (P x keep),
+// and with rhod its tangent in *Rtd: d(U sqrt(l)) = dU sqrt(l) + U dl / (2 sqrt(l)).
+void tatrg_ctx::factor(const double* rho, int64_t P, int kind, DMat& Rt, const double* rhod,
+                       DMat* Rtd) {
   const int64_t ell = std::min(width(), P);
   SvdResult e;
+  Engine::SvdTan et;
   if (ell >= P) {
     e = eng.svd(rho, P, P);
+    if (rhod) et = eng.svd_tan(rhod, P, P, e, keep_count(e.s, 1e-14, ell), multiplet_groups(e.s, tau));
   } else {
     DevBuf om(P * ell * sizeof(double), stream);
     gaussian(p.seed, stream_id(step, kind), replica, P * ell, om.d(), stream);
-    e = eng.rsvd_psd(rho, P, ell, p.q, om.d());
+    if (rhod) {
+      Engine::RsvdT r = eng.rsvd_psd_t(rho, rhod, P, ell, p.q, om.d(), tau);
+      e = std::move(r.e);
+      et = std::move(r.t);
+    } else {
+      e = eng.rsvd_psd(rho, P, ell, p.q, om.d());
+    }
   }
   int keep = keep_count(e.s, 1e-14, ell);
   TATRG_CHECK(keep >= 1, TATRG_ENUMERIC, "squeezer Gram is zero");
@@ -264,7 +384,18 @@ void tatrg_ctx::factor(const double* rho, int64_t P, int kind, DMat& Rt) {
   for (auto& x : sq) x = std::sqrt(std::max(x, 0.0));
   DevBuf sqd(keep * sizeof(double), stream);
   TATRG_CUDA(cudaMemcpyAsync(sqd.d(), sq.data(), keep * sizeof(double), cudaMemcpyHostToDevice, stream));
-  scale_axis(Rt.p(), sqd.d(), P, keep, 1, 1, stream);
+  if (rhod) {
+    std::vector<double> dsq(keep);
+    for (int i = 0; i < keep; ++i) dsq[i] = et.s[i] / (2.0 * sq[i]);
+    DevBuf dsqd = eng.upload(dsq);
+    Rtd->buf = dalloc(P * keep, stream);
+    Rtd->rows = P;
+    Rtd->cols = keep;
+    copy_modes(Rtd->p(), et.U.p(), modes({{P, et.U.cols, keep}, {keep, 1, 1}}), 1.0, stream);
+    scale_axis_tan(Rt.p(), Rtd->p(), sqd.d(), dsqd.d(), P, keep, 1, 1, stream);
+  } else {
+    scale_axis(Rt.p(), sqd.d(), P, keep, 1, 1, stream);
+  }
   TATRG_CUDA(cudaStreamSynchronize(stream));
 }
 
@@ -303,6 +434,28 @@ void tatrg_ctx::rg_step() {
     count(sg, g);
     eng.gemm(g, a, b, c);
   };
+  // Tangent mode: every bilinear contraction c = g(a, b) also gives dc = g(da, b) + g(a, db);
+  // a null tangent is a constant operand.
+  const bool T = tan_on;
+  TATRG_CHECK(!T || !split, TATRG_EINVAL, "tangent runs are FP64");
+  auto run2 = [&](Stage sg, const GemmDesc& g, const double* a, const double* da, const double* b,
+                  const double* db, double* c, double* dc) {
+    run(sg, g, a, b, c);
+    if (!T) return;
+    GemmDesc g2 = g;
+    g2.beta = 0.0;
+    if (da) {
+      eng.gemm(g2, da, b, dc);
+      g2.beta = 1.0;
+    }
+    if (db) {
+      eng.gemm(g2, a, db, dc);
+      g2.beta = 1.0;
+    }
+    TATRG_CHECK(g2.beta == 1.0, TATRG_EINVAL, "tangent contraction without a tangent operand");
+  };
+  auto tp = [&](const DevBuf& b) -> double* { return T ? b.d() : nullptr; };
+  auto tpm = [&](const DMat& b) -> double* { return T ? b.p() : nullptr; };
 
   const int g = d - 2;
   const int64_t D0 = D[0];
@@ -316,46 +469,73 @@ void tatrg_ctx::rg_step() {
   DevBuf As(D0 * I * Da_ * sizeof(double), st), Bs(Da_ * D0 * I * sizeof(double), st);
   TATRG_CUDA(cudaMemcpyAsync(As.d(), A.d(), As.bytes(), cudaMemcpyDeviceToDevice, st));
   TATRG_CUDA(cudaMemcpyAsync(Bs.d(), B.d(), Bs.bytes(), cudaMemcpyDeviceToDevice, st));
-  scale_axis(As.d(), sdev.d(), D0 * I, Da_, 1, 1, st);  // A[k,i,b] s_b
-  scale_axis(Bs.d(), sdev.d(), 1, Da_, D0 * I, 1, st);  // s_a B[a,k,j]
+  DevBuf Asd = tbuf(D0 * I * Da_), Bsd = tbuf(Da_ * D0 * I);
+  if (T) {
+    TATRG_CUDA(cudaMemcpyAsync(Asd.d(), Ad.d(), As.bytes(), cudaMemcpyDeviceToDevice, st));
+    TATRG_CUDA(cudaMemcpyAsync(Bsd.d(), Bd.d(), Bs.bytes(), cudaMemcpyDeviceToDevice, st));
+    scale_axis_tan(As.d(), Asd.d(), sdev.d(), sdd.d(), D0 * I, Da_, 1, 1, st);
+    scale_axis_tan(Bs.d(), Bsd.d(), sdev.d(), sdd.d(), 1, Da_, D0 * I, 1, st);
+  } else {
+    scale_axis(As.d(), sdev.d(), D0 * I, Da_, 1, 1, st);  // A[k,i,b] s_b
+    scale_axis(Bs.d(), sdev.d(), 1, Da_, D0 * I, 1, st);  // s_a B[a,k,j]
+  }
   const int64_t rows = Da_ * I;
   const int64_t ell = std::min(width(), rows);
   SvdResult sw;
+  Engine::SvdTan swt;  // tangent mode: tangents of the leading singular triplets
   info.swap_exact = 0;
   if (ell >= rows) {
     // dense Mid[(a,i),(b,j)] = sum_k Bs[a,k,j] As[k,i,b], one contraction per (a, b)
     info.swap_exact = 1;
-    DevBuf mid(rows * rows * sizeof(double), st);
+    DevBuf mid(rows * rows * sizeof(double), st), midd = tbuf(rows * rows);
     for (int64_t a = 0; a < Da_; ++a)
       for (int64_t b = 0; b < Da_; ++b) {
         GemmDesc gm = G(modes({{I, Da_, rows}}), modes({{I, 1, 1}}), modes({{D0, I * Da_, I}}));
-        run(ST_SWAP, gm, As.d() + b, Bs.d() + a * D0 * I, mid.d() + a * I * rows + b * I);
+        const int64_t oa = b, ob = a * D0 * I, oc = a * I * rows + b * I;
+        run2(ST_SWAP, gm, As.d() + oa, T ? Asd.d() + oa : nullptr, Bs.d() + ob, T ? Bsd.d() + ob : nullptr,
+             mid.d() + oc, T ? midd.d() + oc : nullptr);
       }
     sw = eng.svd(mid.d(), rows, rows);
+    if (T) swt = eng.svd_tan(midd.d(), rows, rows, sw, keep_count(sw.s, 1e-14, sw.r), multiplet_groups(sw.s, tau));
   } else {
     DevBuf om(rows * ell * sizeof(double), st);
     gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st);
     // M X: W[a,k,b,p] = sum_j Bs[a,k,j] X[(b,j),p];  Y[(a,i),p] = sum_{k,b} As[k,i,b] W[a,k,b,p]
-    auto apply = [&](const double* X, int64_t w, double* Y) {
+    // (with any pair of factors Ap, Bp in place of As, Bs; beta = 1 accumulates into Y)
+    auto apply_g = [&](const double* Ap, const double* Bp, const double* X, int64_t w, double* Y,
+                       double beta) {
       DevBuf W(Da_ * D0 * Da_ * w * sizeof(double), st);
       run(ST_SWAP,
           G(modes({{Da_ * D0, I, Da_ * w}}), modes({{Da_, I * w, w}, {w, 1, 1}}), modes({{I, 1, w}})),
-          Bs.d(), X, W.d());
+          Bp, X, W.d());
       run(ST_SWAP,
           G(modes({{I, Da_, w}}), modes({{Da_, D0 * Da_ * w, I * w}, {w, 1, 1}}),
-            modes({{D0, I * Da_, Da_ * w}, {Da_, 1, w}})),
-          As.d(), W.d(), Y);
+            modes({{D0, I * Da_, Da_ * w}, {Da_, 1, w}}), 1.0, beta),
+          Ap, W.d(), Y);
     };
     // M^T X: W[a,k,b,p] = sum_i As[k,i,b] X[(a,i),p];  Z[(b,j),p] = sum_{a,k} Bs[a,k,j] W[a,k,b,p]
-    auto rapply = [&](const double* X, int64_t w, double* Z) {
+    auto rapply_g = [&](const double* Ap, const double* Bp, const double* X, int64_t w, double* Z,
+                        double beta) {
       DevBuf W(Da_ * D0 * Da_ * w * sizeof(double), st);
       run(ST_SWAP,
           G(modes({{D0, I * Da_, Da_ * w}, {Da_, 1, w}}), modes({{Da_, I * w, D0 * Da_ * w}, {w, 1, 1}}),
             modes({{I, Da_, w}})),
-          As.d(), X, W.d());
+          Ap, X, W.d());
       run(ST_SWAP,
-          G(modes({{I, 1, w}}), modes({{Da_, w, I * w}, {w, 1, 1}}), modes({{Da_ * D0, I, Da_ * w}})),
-          Bs.d(), W.d(), Z);
+          G(modes({{I, 1, w}}), modes({{Da_, w, I * w}, {w, 1, 1}}), modes({{Da_ * D0, I, Da_ * w}}), 1.0,
+            beta),
+          Bp, W.d(), Z);
+    };
+    auto apply = [&](const double* X, int64_t w, double* Y) { apply_g(As.d(), Bs.d(), X, w, Y, 0.0); };
+    auto rapply = [&](const double* X, int64_t w, double* Z) { rapply_g(As.d(), Bs.d(), X, w, Z, 0.0); };
+    // dM X = dAs-part + dBs-part (Mid is bilinear in As, Bs)
+    auto apply_d = [&](const double* X, int64_t w, double* Y) {
+      apply_g(Asd.d(), Bs.d(), X, w, Y, 0.0);
+      apply_g(As.d(), Bsd.d(), X, w, Y, 1.0);
+    };
+    auto rapply_d = [&](const double* X, int64_t w, double* Z) {
+      rapply_g(Asd.d(), Bs.d(), X, w, Z, 0.0);
+      rapply_g(As.d(), Bsd.d(), X, w, Z, 1.0);
     };
     // Compressed randomized SVD.  Mid = L R with the inner index (a, k, b):
     //   (R x)[a,k,b] = sum_j Bs[a,k,j] x[(b,j)],  (L w)[(a,i)] = sum_{k,b} As[k,i,b] w[a,k,b];
@@ -367,7 +547,7 @@ void tatrg_ctx::rg_step() {
     const int64_t nin = D0 * Da_;
     const int64_t nL = Da_ * nin;  // rows of an inner panel [a][k][b]
     bool done = false;
-    if (nL > ell) {
+    if (nL > ell && !T) {  // tangent runs take the explicit iteration (the same subspaces)
       DevBuf GA(nin * nin * sizeof(double), st), GB(nin * nin * sizeof(double), st);
       run(ST_SWAP,
           G(modes({{D0, I * Da_, Da_ * nin}, {Da_, 1, nin}}), modes({{D0, I * Da_, Da_}, {Da_, 1, 1}}),
@@ -448,7 +628,13 @@ void tatrg_ctx::rg_step() {
         om = DevBuf(rows * ell * sizeof(double), st);
         gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st);
       }
-      sw = eng.rsvd(apply, rapply, rows, rows, ell, p.q, om.d());
+      if (T) {
+        Engine::RsvdT r = eng.rsvd_t(apply, rapply, apply_d, rapply_d, rows, rows, ell, p.q, om.d(), tau);
+        sw = std::move(r.e);
+        swt = std::move(r.t);
+      } else {
+        sw = eng.rsvd(apply, rapply, rows, rows, ell, p.q, om.d());
+      }
     }
   }
   const int64_t Dg = multiplet_cut(sw.s, keep_count(sw.s, 1e-14, chi()), tau);
@@ -459,12 +645,21 @@ void tatrg_ctx::rg_step() {
   DevBuf X(rows * Dg * sizeof(double), st), Y(rows * Dg * sizeof(double), st);
   copy_modes(X.d(), sw.U.p(), modes({{rows, sw.U.cols, Dg}, {Dg, 1, 1}}), 1.0, st);
   copy_modes(Y.d(), sw.V.p(), modes({{rows, sw.V.cols, Dg}, {Dg, 1, 1}}), 1.0, st);
-  fix_sign_cols(X.d(), rows, int(Dg), Y.d(), rows);
+  DevBuf Xd = tbuf(rows * Dg), Yd = tbuf(rows * Dg), sigdd;
+  if (T) {
+    TATRG_CHECK(swt.U.cols >= Dg, TATRG_ENUMERIC, "bond swap: tangent of a cut below the rounding floor");
+    copy_modes(Xd.d(), swt.U.p(), modes({{rows, swt.U.cols, Dg}, {Dg, 1, 1}}), 1.0, st);
+    copy_modes(Yd.d(), swt.V.p(), modes({{rows, swt.V.cols, Dg}, {Dg, 1, 1}}), 1.0, st);
+    sigdd = eng.upload(std::vector<double>(swt.s.begin(), swt.s.begin() + Dg));
+  }
+  fix_sign_cols(X.d(), rows, int(Dg), Y.d(), rows, tp(Xd), tp(Yd));
   std::vector<double> sig(sw.s.begin(), sw.s.begin() + Dg);
   DevBuf sigd(Dg * sizeof(double), st);
   TATRG_CUDA(cudaMemcpyAsync(sigd.d(), sig.data(), Dg * sizeof(double), cudaMemcpyHostToDevice, st));
   As.release();
   Bs.release();
+  Asd.release();
+  Bsd.release();
 
   // ======================== triad isometries and tensors (Eqs. 2-4) ========================
   tm.mark(1);
@@ -473,202 +668,248 @@ void tatrg_ctx::rg_step() {
   DevBuf Xs(nx * sizeof(double), st), Ys(nx * sizeof(double), st);
   TATRG_CUDA(cudaMemcpyAsync(Xs.d(), X.d(), nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
   TATRG_CUDA(cudaMemcpyAsync(Ys.d(), Y.d(), nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  scale_axis(Xs.d(), sigd.d(), Da_ * Gd * Ds, Dg, 1, 2, st);
-  scale_axis(Ys.d(), sigd.d(), Da_ * Gd * Ds, Dg, 1, 2, st);
+  DevBuf Xsd = tbuf(nx), Ysd = tbuf(nx);
+  if (T) {
+    TATRG_CUDA(cudaMemcpyAsync(Xsd.d(), Xd.d(), nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    TATRG_CUDA(cudaMemcpyAsync(Ysd.d(), Yd.d(), nx * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    scale_axis_tan(Xs.d(), Xsd.d(), sigd.d(), sigdd.d(), Da_ * Gd * Ds, Dg, 1, 2, st);
+    scale_axis_tan(Ys.d(), Ysd.d(), sigd.d(), sigdd.d(), Da_ * Gd * Ds, Dg, 1, 2, st);
+  } else {
+    scale_axis(Xs.d(), sigd.d(), Da_ * Gd * Ds, Dg, 1, 2, st);
+    scale_axis(Ys.d(), sigd.d(), Da_ * Gd * Ds, Dg, 1, 2, st);
+  }
   const int64_t GSg = Gd * Ds * Dg;
   DevBuf xi_x(Da_ * Da_ * sizeof(double), st), xi_y(Da_ * Da_ * sizeof(double), st);
-  run(ST_TRIAD, G(modes({{Da_, GSg, Da_}}), modes({{Da_, GSg, 1}}), modes({{GSg, 1, 1}})), Xs.d(), X.d(), xi_x.d());
-  run(ST_TRIAD, G(modes({{Da_, GSg, Da_}}), modes({{Da_, GSg, 1}}), modes({{GSg, 1, 1}})), Ys.d(), Y.d(), xi_y.d());
+  DevBuf xi_xd = tbuf(Da_ * Da_), xi_yd = tbuf(Da_ * Da_);
+  run2(ST_TRIAD, G(modes({{Da_, GSg, Da_}}), modes({{Da_, GSg, 1}}), modes({{GSg, 1, 1}})), Xs.d(), tp(Xsd),
+       X.d(), tp(Xd), xi_x.d(), tp(xi_xd));
+  run2(ST_TRIAD, G(modes({{Da_, GSg, Da_}}), modes({{Da_, GSg, 1}}), modes({{GSg, 1, 1}})), Ys.d(), tp(Ysd),
+       Y.d(), tp(Yd), xi_y.d(), tp(xi_yd));
   DevBuf rho_a(Gd * Gd * sizeof(double), st), rho_x(Gd * Gd * sizeof(double), st),
       rho_y(Gd * Gd * sizeof(double), st), rho_d(Gd * Gd * sizeof(double), st);
+  DevBuf rho_ad = tbuf(Gd * Gd), rho_xd = tbuf(Gd * Gd), rho_yd = tbuf(Gd * Gd), rho_dd = tbuf(Gd * Gd);
   {
     // t_a[i0,G,s,a'] = sum_a A[i0,G,s,a] Xi_X[a,a'];  rho_A[G,G'] = sum t_a[i0,G,s,a] A[i0,G',s,a]
-    DevBuf ta(D0 * Gd * Ds * Da_ * sizeof(double), st);
-    run(ST_TRIAD, G(modes({{D0 * Gd * Ds, Da_, Da_}}), modes({{Da_, 1, 1}}), modes({{Da_, 1, Da_}})),
-        A.d(), xi_x.d(), ta.d());
-    run(ST_TRIAD,
-        G(modes({{Gd, Ds * Da_, Gd}}), modes({{Gd, Ds * Da_, 1}}),
-          modes({{D0, Gd * Ds * Da_, Gd * Ds * Da_}, {Ds * Da_, 1, 1}})),
-        ta.d(), A.d(), rho_a.d());
+    DevBuf ta(D0 * Gd * Ds * Da_ * sizeof(double), st), tad = tbuf(D0 * Gd * Ds * Da_);
+    run2(ST_TRIAD, G(modes({{D0 * Gd * Ds, Da_, Da_}}), modes({{Da_, 1, 1}}), modes({{Da_, 1, Da_}})),
+         A.d(), tp(Ad), xi_x.d(), tp(xi_xd), ta.d(), tp(tad));
+    run2(ST_TRIAD,
+         G(modes({{Gd, Ds * Da_, Gd}}), modes({{Gd, Ds * Da_, 1}}),
+           modes({{D0, Gd * Ds * Da_, Gd * Ds * Da_}, {Ds * Da_, 1, 1}})),
+         ta.d(), tp(tad), A.d(), tp(Ad), rho_a.d(), tp(rho_ad));
     // rho_X[G,G'] = sum_{a,s,g} Xs[a,G,s,g] X[a,G',s,g]  (and rho_Y)
     GemmDesc gx = G(modes({{Gd, Ds * Dg, Gd}}), modes({{Gd, Ds * Dg, 1}}),
                     modes({{Da_, GSg, GSg}, {Ds * Dg, 1, 1}}));
-    run(ST_TRIAD, gx, Xs.d(), X.d(), rho_x.d());
-    run(ST_TRIAD, gx, Ys.d(), Y.d(), rho_y.d());
+    run2(ST_TRIAD, gx, Xs.d(), tp(Xsd), X.d(), tp(Xd), rho_x.d(), tp(rho_xd));
+    run2(ST_TRIAD, gx, Ys.d(), tp(Ysd), Y.d(), tp(Yd), rho_y.d(), tp(rho_yd));
     // t_d[b',j0,G,s] = sum_b Xi_Y[b,b'] D[b,j0,G,s];  rho_D = sum t_d[b,j0,G,s] D[b,j0,G',s]
-    DevBuf td(Da_ * D0 * Gd * Ds * sizeof(double), st);
+    DevBuf td(Da_ * D0 * Gd * Ds * sizeof(double), st), tdd = tbuf(Da_ * D0 * Gd * Ds);
     const int64_t JGS = D0 * Gd * Ds;
-    run(ST_TRIAD, G(modes({{Da_, 1, JGS}}), modes({{JGS, 1, 1}}), modes({{Da_, Da_, JGS}})),
-        xi_y.d(), B.d(), td.d());
-    run(ST_TRIAD,
-        G(modes({{Gd, Ds, Gd}}), modes({{Gd, Ds, 1}}), modes({{Da_ * D0, Gd * Ds, Gd * Ds}, {Ds, 1, 1}})),
-        td.d(), B.d(), rho_d.d());
+    run2(ST_TRIAD, G(modes({{Da_, 1, JGS}}), modes({{JGS, 1, 1}}), modes({{Da_, Da_, JGS}})),
+         xi_y.d(), tp(xi_yd), B.d(), tp(Bd), td.d(), tp(tdd));
+    run2(ST_TRIAD,
+         G(modes({{Gd, Ds, Gd}}), modes({{Gd, Ds, 1}}), modes({{Da_ * D0, Gd * Ds, Gd * Ds}, {Ds, 1, 1}})),
+         td.d(), tp(tdd), B.d(), tp(Bd), rho_d.d(), tp(rho_dd));
   }
   Xs.release();
   Ys.release();
-  DMat UA = isometry(rho_a.d(), Gd, KIND_TRIAD_A, nullptr);
-  DMat UX = isometry(rho_x.d(), Gd, KIND_TRIAD_X, nullptr);
-  DMat UY = isometry(rho_y.d(), Gd, KIND_TRIAD_Y, nullptr);
-  DMat UD = isometry(rho_d.d(), Gd, KIND_TRIAD_D, nullptr);
+  Xsd.release();
+  Ysd.release();
+  DMat UAd, UXd, UYd, UDd;
+  DMat UA = isometry(rho_a.d(), Gd, KIND_TRIAD_A, nullptr, tp(rho_ad), &UAd);
+  DMat UX = isometry(rho_x.d(), Gd, KIND_TRIAD_X, nullptr, tp(rho_xd), &UXd);
+  DMat UY = isometry(rho_y.d(), Gd, KIND_TRIAD_Y, nullptr, tp(rho_yd), &UYd);
+  DMat UD = isometry(rho_d.d(), Gd, KIND_TRIAD_D, nullptr, tp(rho_dd), &UDd);
   const int64_t KA = UA.cols, KX = UX.cols, KY = UY.cols, KD = UD.cols;
   // E[i0,kA,s,a] = sum_G A[i0,G,s,a] UA[G,kA]
   DevBuf E(D0 * KA * Ds * Da_ * sizeof(double), st), F(Da_ * KX * Ds * Dg * sizeof(double), st),
       Gt(Da_ * KY * Ds * Dg * sizeof(double), st), H(D0 * KD * Ds * Da_ * sizeof(double), st);
-  run(ST_TRIAD,
-      G(modes({{D0, Gd * Ds * Da_, KA * Ds * Da_}, {Ds * Da_, 1, 1}}), modes({{KA, 1, Ds * Da_}}),
-        modes({{Gd, Ds * Da_, KA}})),
-      A.d(), UA.p(), E.d());
+  DevBuf Ed = tbuf(D0 * KA * Ds * Da_), Fd = tbuf(Da_ * KX * Ds * Dg), Gtd = tbuf(Da_ * KY * Ds * Dg),
+         Hd = tbuf(D0 * KD * Ds * Da_);
+  run2(ST_TRIAD,
+       G(modes({{D0, Gd * Ds * Da_, KA * Ds * Da_}, {Ds * Da_, 1, 1}}), modes({{KA, 1, Ds * Da_}}),
+         modes({{Gd, Ds * Da_, KA}})),
+       A.d(), tp(Ad), UA.p(), tpm(UAd), E.d(), tp(Ed));
   // F[a,kX,s,g] = sum_G X[a,G,s,g] UX[G,kX] sigma_g ;  G[b,kY,s,g] likewise with Y
-  run(ST_TRIAD,
-      G(modes({{Da_, GSg, KX * Ds * Dg}, {Ds * Dg, 1, 1}}), modes({{KX, 1, Ds * Dg}}),
-        modes({{Gd, Ds * Dg, KX}})),
-      X.d(), UX.p(), F.d());
-  scale_axis(F.d(), sigd.d(), Da_ * KX * Ds, Dg, 1, 1, st);
-  run(ST_TRIAD,
-      G(modes({{Da_, GSg, KY * Ds * Dg}, {Ds * Dg, 1, 1}}), modes({{KY, 1, Ds * Dg}}),
-        modes({{Gd, Ds * Dg, KY}})),
-      Y.d(), UY.p(), Gt.d());
+  run2(ST_TRIAD,
+       G(modes({{Da_, GSg, KX * Ds * Dg}, {Ds * Dg, 1, 1}}), modes({{KX, 1, Ds * Dg}}),
+         modes({{Gd, Ds * Dg, KX}})),
+       X.d(), tp(Xd), UX.p(), tpm(UXd), F.d(), tp(Fd));
+  if (T) scale_axis_tan(F.d(), Fd.d(), sigd.d(), sigdd.d(), Da_ * KX * Ds, Dg, 1, 1, st);
+  else scale_axis(F.d(), sigd.d(), Da_ * KX * Ds, Dg, 1, 1, st);
+  run2(ST_TRIAD,
+       G(modes({{Da_, GSg, KY * Ds * Dg}, {Ds * Dg, 1, 1}}), modes({{KY, 1, Ds * Dg}}),
+         modes({{Gd, Ds * Dg, KY}})),
+       Y.d(), tp(Yd), UY.p(), tpm(UYd), Gt.d(), tp(Gtd));
   // H[j0,kD,s,b] = sum_G D[b,j0,G,s] UD[G,kD]
-  run(ST_TRIAD,
-      G(modes({{D0, Gd * Ds, KD * Ds * Da_}, {Ds, 1, Da_}, {Da_, D0 * Gd * Ds, 1}}),
-        modes({{KD, 1, Ds * Da_}}), modes({{Gd, Ds, KD}})),
-      B.d(), UD.p(), H.d());
+  run2(ST_TRIAD,
+       G(modes({{D0, Gd * Ds, KD * Ds * Da_}, {Ds, 1, Da_}, {Da_, D0 * Gd * Ds, 1}}),
+         modes({{KD, 1, Ds * Da_}}), modes({{Gd, Ds, KD}})),
+       B.d(), tp(Bd), UD.p(), tpm(UDd), H.d(), tp(Hd));
   X.release();
   Y.release();
+  Xd.release();
+  Yd.release();
 
   // ============================ squeezers (Eq. 5) ============================
   tm.mark(2);
   stage_prec(ST_SQUEEZE);
   std::vector<DMat> Ms(d - 1), Nts(d - 1);  // M[(a,b),k] and N^T[(a,b),k]
+  std::vector<DMat> Msd(d - 1), Ntsd(d - 1);  // their tangents (tangent mode)
   std::vector<int64_t> Kn(d - 1, 0);
   spec_sq.assign(d - 1, {});
   {
     DevBuf om_d(Da_ * Da_ * sizeof(double), st), om_y(Dg * Dg * sizeof(double), st),
         om_a(Da_ * Da_ * sizeof(double), st), om_x(Dg * Dg * sizeof(double), st);
+    DevBuf om_dd = tbuf(Da_ * Da_), om_yd = tbuf(Dg * Dg), om_ad = tbuf(Da_ * Da_), om_xd = tbuf(Dg * Dg);
     const int64_t JKS = D0 * KD * Ds, IKS = D0 * KA * Ds;
-    run(ST_SQUEEZE, G(modes({{Da_, 1, Da_}}), modes({{Da_, 1, 1}}), modes({{JKS, Da_, Da_}})), H.d(), H.d(), om_d.d());
-    run(ST_SQUEEZE, G(modes({{Da_, 1, Da_}}), modes({{Da_, 1, 1}}), modes({{IKS, Da_, Da_}})), E.d(), E.d(), om_a.d());
+    run2(ST_SQUEEZE, G(modes({{Da_, 1, Da_}}), modes({{Da_, 1, 1}}), modes({{JKS, Da_, Da_}})), H.d(), tp(Hd),
+         H.d(), tp(Hd), om_d.d(), tp(om_dd));
+    run2(ST_SQUEEZE, G(modes({{Da_, 1, Da_}}), modes({{Da_, 1, 1}}), modes({{IKS, Da_, Da_}})), E.d(), tp(Ed),
+         E.d(), tp(Ed), om_a.d(), tp(om_ad));
     {
       const int64_t KSg = KY * Ds * Dg;
-      DevBuf t(Da_ * KSg * sizeof(double), st);
-      run(ST_SQUEEZE, G(modes({{Da_, 1, KSg}}), modes({{KSg, 1, 1}}), modes({{Da_, Da_, KSg}})), om_d.d(), Gt.d(), t.d());
-      run(ST_SQUEEZE, G(modes({{Dg, 1, Dg}}), modes({{Dg, 1, 1}}), modes({{Da_ * KY * Ds, Dg, Dg}})), t.d(), Gt.d(), om_y.d());
+      DevBuf t(Da_ * KSg * sizeof(double), st), td = tbuf(Da_ * KSg);
+      run2(ST_SQUEEZE, G(modes({{Da_, 1, KSg}}), modes({{KSg, 1, 1}}), modes({{Da_, Da_, KSg}})), om_d.d(),
+           tp(om_dd), Gt.d(), tp(Gtd), t.d(), tp(td));
+      run2(ST_SQUEEZE, G(modes({{Dg, 1, Dg}}), modes({{Dg, 1, 1}}), modes({{Da_ * KY * Ds, Dg, Dg}})), t.d(),
+           tp(td), Gt.d(), tp(Gtd), om_y.d(), tp(om_yd));
     }
     {
       const int64_t KSg = KX * Ds * Dg;
-      DevBuf t(Da_ * KSg * sizeof(double), st);
-      run(ST_SQUEEZE, G(modes({{Da_, 1, KSg}}), modes({{KSg, 1, 1}}), modes({{Da_, Da_, KSg}})), om_a.d(), F.d(), t.d());
-      run(ST_SQUEEZE, G(modes({{Dg, 1, Dg}}), modes({{Dg, 1, 1}}), modes({{Da_ * KX * Ds, Dg, Dg}})), t.d(), F.d(), om_x.d());
+      DevBuf t(Da_ * KSg * sizeof(double), st), td = tbuf(Da_ * KSg);
+      run2(ST_SQUEEZE, G(modes({{Da_, 1, KSg}}), modes({{KSg, 1, 1}}), modes({{Da_, Da_, KSg}})), om_a.d(),
+           tp(om_ad), F.d(), tp(Fd), t.d(), tp(td));
+      run2(ST_SQUEEZE, G(modes({{Dg, 1, Dg}}), modes({{Dg, 1, 1}}), modes({{Da_ * KX * Ds, Dg, Dg}})), t.d(),
+           tp(td), F.d(), tp(Fd), om_x.d(), tp(om_xd));
     }
     // Fy[a,kX,s,g'] = sum_g F[..,g] Om_Y[g,g'];  Gx likewise with Om_X
     DevBuf Fy(Da_ * KX * Ds * Dg * sizeof(double), st), Gx(Da_ * KY * Ds * Dg * sizeof(double), st);
-    run(ST_SQUEEZE, G(modes({{Da_ * KX * Ds, Dg, Dg}}), modes({{Dg, 1, 1}}), modes({{Dg, 1, Dg}})), F.d(), om_y.d(), Fy.d());
-    run(ST_SQUEEZE, G(modes({{Da_ * KY * Ds, Dg, Dg}}), modes({{Dg, 1, 1}}), modes({{Dg, 1, Dg}})), Gt.d(), om_x.d(), Gx.d());
+    DevBuf Fyd = tbuf(Da_ * KX * Ds * Dg), Gxd = tbuf(Da_ * KY * Ds * Dg);
+    run2(ST_SQUEEZE, G(modes({{Da_ * KX * Ds, Dg, Dg}}), modes({{Dg, 1, 1}}), modes({{Dg, 1, Dg}})), F.d(),
+         tp(Fd), om_y.d(), tp(om_yd), Fy.d(), tp(Fyd));
+    run2(ST_SQUEEZE, G(modes({{Da_ * KY * Ds, Dg, Dg}}), modes({{Dg, 1, 1}}), modes({{Dg, 1, Dg}})), Gt.d(),
+         tp(Gtd), om_x.d(), tp(om_xd), Gx.d(), tp(Gxd));
 
     const int64_t P = Ds * Ds;
-    std::vector<DevBuf> rhoL(d - 1), rhoR(d - 1);
+    std::vector<DevBuf> rhoL(d - 1), rhoR(d - 1), rhoLd(d - 1), rhoRd(d - 1);
     // separate leg (position d-1)
     {
       DevBuf eps(Ds * Da_ * Ds * Da_ * sizeof(double), st), phi(Da_ * Ds * Da_ * Ds * sizeof(double), st);
-      run(ST_SQUEEZE, G(modes({{Ds * Da_, 1, Ds * Da_}}), modes({{Ds * Da_, 1, 1}}), modes({{D0 * KA, Ds * Da_, Ds * Da_}})),
-          E.d(), E.d(), eps.d());
-      run(ST_SQUEEZE,
-          G(modes({{Da_, KX * Ds * Dg, Ds * Da_ * Ds}, {Ds, Dg, Da_ * Ds}}),
-            modes({{Da_, KX * Ds * Dg, Ds}, {Ds, Dg, 1}}), modes({{KX, Ds * Dg, Ds * Dg}, {Dg, 1, 1}})),
-          Fy.d(), F.d(), phi.d());
+      DevBuf epsd = tbuf(Ds * Da_ * Ds * Da_), phid = tbuf(Da_ * Ds * Da_ * Ds);
+      run2(ST_SQUEEZE,
+           G(modes({{Ds * Da_, 1, Ds * Da_}}), modes({{Ds * Da_, 1, 1}}), modes({{D0 * KA, Ds * Da_, Ds * Da_}})),
+           E.d(), tp(Ed), E.d(), tp(Ed), eps.d(), tp(epsd));
+      run2(ST_SQUEEZE,
+           G(modes({{Da_, KX * Ds * Dg, Ds * Da_ * Ds}, {Ds, Dg, Da_ * Ds}}),
+             modes({{Da_, KX * Ds * Dg, Ds}, {Ds, Dg, 1}}), modes({{KX, Ds * Dg, Ds * Dg}, {Dg, 1, 1}})),
+           Fy.d(), tp(Fyd), F.d(), tp(Fd), phi.d(), tp(phid));
       rhoL[d - 2] = DevBuf(P * P * sizeof(double), st);
-      run(ST_SQUEEZE,
-          G(modes({{Ds, Da_ * Ds * Da_, Ds * Ds * Ds}, {Ds, Da_, Ds}}),
-            modes({{Ds, Da_ * Ds, Ds * Ds}, {Ds, 1, 1}}),
-            modes({{Da_, Ds * Da_, Ds * Da_ * Ds}, {Da_, 1, Ds}})),
-          eps.d(), phi.d(), rhoL[d - 2].d());
+      rhoLd[d - 2] = tbuf(P * P);
+      run2(ST_SQUEEZE,
+           G(modes({{Ds, Da_ * Ds * Da_, Ds * Ds * Ds}, {Ds, Da_, Ds}}),
+             modes({{Ds, Da_ * Ds, Ds * Ds}, {Ds, 1, 1}}),
+             modes({{Da_, Ds * Da_, Ds * Da_ * Ds}, {Da_, 1, Ds}})),
+           eps.d(), tp(epsd), phi.d(), tp(phid), rhoL[d - 2].d(), tp(rhoLd[d - 2]));
       DevBuf gam(Da_ * Ds * Da_ * Ds * sizeof(double), st), eta(Ds * Da_ * Ds * Da_ * sizeof(double), st);
-      run(ST_SQUEEZE,
-          G(modes({{Da_, KY * Ds * Dg, Ds * Da_ * Ds}, {Ds, Dg, Da_ * Ds}}),
-            modes({{Da_, KY * Ds * Dg, Ds}, {Ds, Dg, 1}}), modes({{KY, Ds * Dg, Ds * Dg}, {Dg, 1, 1}})),
-          Gx.d(), Gt.d(), gam.d());
-      run(ST_SQUEEZE, G(modes({{Ds * Da_, 1, Ds * Da_}}), modes({{Ds * Da_, 1, 1}}), modes({{D0 * KD, Ds * Da_, Ds * Da_}})),
-          H.d(), H.d(), eta.d());
+      DevBuf gamd = tbuf(Da_ * Ds * Da_ * Ds), etad = tbuf(Ds * Da_ * Ds * Da_);
+      run2(ST_SQUEEZE,
+           G(modes({{Da_, KY * Ds * Dg, Ds * Da_ * Ds}, {Ds, Dg, Da_ * Ds}}),
+             modes({{Da_, KY * Ds * Dg, Ds}, {Ds, Dg, 1}}), modes({{KY, Ds * Dg, Ds * Dg}, {Dg, 1, 1}})),
+           Gx.d(), tp(Gxd), Gt.d(), tp(Gtd), gam.d(), tp(gamd));
+      run2(ST_SQUEEZE,
+           G(modes({{Ds * Da_, 1, Ds * Da_}}), modes({{Ds * Da_, 1, 1}}), modes({{D0 * KD, Ds * Da_, Ds * Da_}})),
+           H.d(), tp(Hd), H.d(), tp(Hd), eta.d(), tp(etad));
       rhoR[d - 2] = DevBuf(P * P * sizeof(double), st);
+      rhoRd[d - 2] = tbuf(P * P);
       // rho_R[(a,b),(a',b')] = sum_{b,b'} gam[be,a,be',a'] eta[b,be,b',be']
-      run(ST_SQUEEZE,
-          G(modes({{Ds, Da_ * Ds, Ds * Ds * Ds}, {Ds, 1, Ds}}),
-            modes({{Ds, Da_ * Ds * Da_, Ds * Ds}, {Ds, Da_, 1}}),
-            modes({{Da_, Ds * Da_ * Ds, Ds * Da_}, {Da_, Ds, 1}})),
-          gam.d(), eta.d(), rhoR[d - 2].d());
+      run2(ST_SQUEEZE,
+           G(modes({{Ds, Da_ * Ds, Ds * Ds * Ds}, {Ds, 1, Ds}}),
+             modes({{Ds, Da_ * Ds * Da_, Ds * Ds}, {Ds, Da_, 1}}),
+             modes({{Da_, Ds * Da_ * Ds, Ds * Da_}, {Da_, Ds, 1}})),
+           gam.d(), tp(gamd), eta.d(), tp(etad), rhoR[d - 2].d(), tp(rhoRd[d - 2]));
     }
     if (g > 0) {
       // Env_L[kA,kA',kX,kX'] = sum_{a,a'} P_E[kA,kA',a,a'] P_F[a,a',kX,kX']
       DevBuf pe(KA * KA * Da_ * Da_ * sizeof(double), st), pf(Da_ * Da_ * KX * KX * sizeof(double), st);
-      run(ST_SQUEEZE,
-          G(modes({{KA, Ds * Da_, KA * Da_ * Da_}, {Da_, 1, Da_}}), modes({{KA, Ds * Da_, Da_ * Da_}, {Da_, 1, 1}}),
-            modes({{D0, KA * Ds * Da_, KA * Ds * Da_}, {Ds, Da_, Da_}})),
-          E.d(), E.d(), pe.d());
-      run(ST_SQUEEZE,
-          G(modes({{Da_, KX * Ds * Dg, Da_ * KX * KX}, {KX, Ds * Dg, KX}}),
-            modes({{Da_, KX * Ds * Dg, KX * KX}, {KX, Ds * Dg, 1}}), modes({{Ds * Dg, 1, 1}})),
-          Fy.d(), F.d(), pf.d());
-      DevBuf envL(KA * KA * KX * KX * sizeof(double), st);
-      run(ST_SQUEEZE, G(modes({{KA * KA, Da_ * Da_, KX * KX}}), modes({{KX * KX, 1, 1}}), modes({{Da_ * Da_, 1, KX * KX}})),
-          pe.d(), pf.d(), envL.d());
+      DevBuf ped = tbuf(KA * KA * Da_ * Da_), pfd = tbuf(Da_ * Da_ * KX * KX);
+      run2(ST_SQUEEZE,
+           G(modes({{KA, Ds * Da_, KA * Da_ * Da_}, {Da_, 1, Da_}}), modes({{KA, Ds * Da_, Da_ * Da_}, {Da_, 1, 1}}),
+             modes({{D0, KA * Ds * Da_, KA * Ds * Da_}, {Ds, Da_, Da_}})),
+           E.d(), tp(Ed), E.d(), tp(Ed), pe.d(), tp(ped));
+      run2(ST_SQUEEZE,
+           G(modes({{Da_, KX * Ds * Dg, Da_ * KX * KX}, {KX, Ds * Dg, KX}}),
+             modes({{Da_, KX * Ds * Dg, KX * KX}, {KX, Ds * Dg, 1}}), modes({{Ds * Dg, 1, 1}})),
+           Fy.d(), tp(Fyd), F.d(), tp(Fd), pf.d(), tp(pfd));
+      DevBuf envL(KA * KA * KX * KX * sizeof(double), st), envLd = tbuf(KA * KA * KX * KX);
+      run2(ST_SQUEEZE,
+           G(modes({{KA * KA, Da_ * Da_, KX * KX}}), modes({{KX * KX, 1, 1}}), modes({{Da_ * Da_, 1, KX * KX}})),
+           pe.d(), tp(ped), pf.d(), tp(pfd), envL.d(), tp(envLd));
       DevBuf pg(KY * KY * Da_ * Da_ * sizeof(double), st), ph(Da_ * Da_ * KD * KD * sizeof(double), st);
-      run(ST_SQUEEZE,
-          G(modes({{KY, Ds * Dg, KY * Da_ * Da_}, {Da_, KY * Ds * Dg, Da_}}),
-            modes({{KY, Ds * Dg, Da_ * Da_}, {Da_, KY * Ds * Dg, 1}}), modes({{Ds * Dg, 1, 1}})),
-          Gx.d(), Gt.d(), pg.d());
-      run(ST_SQUEEZE,
-          G(modes({{Da_, 1, Da_ * KD * KD}, {KD, Ds * Da_, KD}}), modes({{Da_, 1, KD * KD}, {KD, Ds * Da_, 1}}),
-            modes({{D0, KD * Ds * Da_, KD * Ds * Da_}, {Ds, Da_, Da_}})),
-          H.d(), H.d(), ph.d());
-      DevBuf envR(KY * KY * KD * KD * sizeof(double), st);
-      run(ST_SQUEEZE, G(modes({{KY * KY, Da_ * Da_, KD * KD}}), modes({{KD * KD, 1, 1}}), modes({{Da_ * Da_, 1, KD * KD}})),
-          pg.d(), ph.d(), envR.d());
+      DevBuf pgd = tbuf(KY * KY * Da_ * Da_), phd = tbuf(Da_ * Da_ * KD * KD);
+      run2(ST_SQUEEZE,
+           G(modes({{KY, Ds * Dg, KY * Da_ * Da_}, {Da_, KY * Ds * Dg, Da_}}),
+             modes({{KY, Ds * Dg, Da_ * Da_}, {Da_, KY * Ds * Dg, 1}}), modes({{Ds * Dg, 1, 1}})),
+           Gx.d(), tp(Gxd), Gt.d(), tp(Gtd), pg.d(), tp(pgd));
+      run2(ST_SQUEEZE,
+           G(modes({{Da_, 1, Da_ * KD * KD}, {KD, Ds * Da_, KD}}), modes({{Da_, 1, KD * KD}, {KD, Ds * Da_, 1}}),
+             modes({{D0, KD * Ds * Da_, KD * Ds * Da_}, {Ds, Da_, Da_}})),
+           H.d(), tp(Hd), H.d(), tp(Hd), ph.d(), tp(phd));
+      DevBuf envR(KY * KY * KD * KD * sizeof(double), st), envRd = tbuf(KY * KY * KD * KD);
+      run2(ST_SQUEEZE,
+           G(modes({{KY * KY, Da_ * Da_, KD * KD}}), modes({{KD * KD, 1, 1}}), modes({{Da_ * Da_, 1, KD * KD}})),
+           pg.d(), tp(pgd), ph.d(), tp(phd), envR.d(), tp(envRd));
       for (int nu = 1; nu <= g; ++nu) {
         const int64_t Dn = D[nu];
         const int64_t Dz = Gd / Dn;  // product of the other group legs (1 when g == 1)
         // stride of leg nu and of the others inside the group index (row-major group legs)
         const int64_t snu = prod(D, nu + 1, 1 + g);
-        auto pairgram = [&](const DMat& U, int64_t K, DevBuf& out) {
+        auto pairgram = [&](const DMat& U, const DMat& Ud_, int64_t K, DevBuf& out, DevBuf& outd) {
           out = DevBuf(Dn * Dn * K * K * sizeof(double), st);
+          outd = tbuf(Dn * Dn * K * K);
           // out[a,a',k,k'] = sum_z U[(..a..z..),k] U[(..a'..z..),k']
           ModeIdx kz;
           if (g == 1) kz = modes({});
           else if (nu == 1) kz = modes({{Dz, K, K}});        // z = leg 2, stride K
           else kz = modes({{Dz, Dn * K, Dn * K}});           // z = leg 1, stride D2*K
-          run(ST_SQUEEZE,
-              G(modes({{Dn, snu * K, Dn * K * K}, {K, 1, K}}), modes({{Dn, snu * K, K * K}, {K, 1, 1}}), kz),
-              U.p(), U.p(), out.d());
+          run2(ST_SQUEEZE,
+               G(modes({{Dn, snu * K, Dn * K * K}, {K, 1, K}}), modes({{Dn, snu * K, K * K}, {K, 1, 1}}), kz),
+               U.p(), tpm(Ud_), U.p(), tpm(Ud_), out.d(), tp(outd));
         };
-        DevBuf ii, jj, kk, ll;
-        pairgram(UA, KA, ii);
-        pairgram(UX, KX, jj);
-        pairgram(UY, KY, kk);
-        pairgram(UD, KD, ll);
+        DevBuf ii, jj, kk, ll, iid, jjd, kkd, lld;
+        pairgram(UA, UAd, KA, ii, iid);
+        pairgram(UX, UXd, KX, jj, jjd);
+        pairgram(UY, UYd, KY, kk, kkd);
+        pairgram(UD, UDd, KD, ll, lld);
         const int64_t Pn = Dn * Dn;
-        DevBuf t(Pn * KX * KX * sizeof(double), st);
-        run(ST_SQUEEZE, G(modes({{Pn, KA * KA, KX * KX}}), modes({{KX * KX, 1, 1}}), modes({{KA * KA, 1, KX * KX}})),
-            ii.d(), envL.d(), t.d());
+        DevBuf t(Pn * KX * KX * sizeof(double), st), td = tbuf(Pn * KX * KX);
+        run2(ST_SQUEEZE,
+             G(modes({{Pn, KA * KA, KX * KX}}), modes({{KX * KX, 1, 1}}), modes({{KA * KA, 1, KX * KX}})),
+             ii.d(), tp(iid), envL.d(), tp(envLd), t.d(), tp(td));
         rhoL[nu - 1] = DevBuf(Pn * Pn * sizeof(double), st);
-        run(ST_SQUEEZE,
-            G(modes({{Dn, Dn * KX * KX, Dn * Dn * Dn}, {Dn, KX * KX, Dn}}),
-              modes({{Dn, Dn * KX * KX, Dn * Dn}, {Dn, KX * KX, 1}}), modes({{KX * KX, 1, 1}})),
-            t.d(), jj.d(), rhoL[nu - 1].d());
-        DevBuf t2(Pn * KD * KD * sizeof(double), st);
-        run(ST_SQUEEZE, G(modes({{Pn, KY * KY, KD * KD}}), modes({{KD * KD, 1, 1}}), modes({{KY * KY, 1, KD * KD}})),
-            kk.d(), envR.d(), t2.d());
+        rhoLd[nu - 1] = tbuf(Pn * Pn);
+        run2(ST_SQUEEZE,
+             G(modes({{Dn, Dn * KX * KX, Dn * Dn * Dn}, {Dn, KX * KX, Dn}}),
+               modes({{Dn, Dn * KX * KX, Dn * Dn}, {Dn, KX * KX, 1}}), modes({{KX * KX, 1, 1}})),
+             t.d(), tp(td), jj.d(), tp(jjd), rhoL[nu - 1].d(), tp(rhoLd[nu - 1]));
+        DevBuf t2(Pn * KD * KD * sizeof(double), st), t2d = tbuf(Pn * KD * KD);
+        run2(ST_SQUEEZE,
+             G(modes({{Pn, KY * KY, KD * KD}}), modes({{KD * KD, 1, 1}}), modes({{KY * KY, 1, KD * KD}})),
+             kk.d(), tp(kkd), envR.d(), tp(envRd), t2.d(), tp(t2d));
         rhoR[nu - 1] = DevBuf(Pn * Pn * sizeof(double), st);
-        run(ST_SQUEEZE,
-            G(modes({{Dn, Dn * KD * KD, Dn * Dn * Dn}, {Dn, KD * KD, Dn}}),
-              modes({{Dn, Dn * KD * KD, Dn * Dn}, {Dn, KD * KD, 1}}), modes({{KD * KD, 1, 1}})),
-            t2.d(), ll.d(), rhoR[nu - 1].d());
+        rhoRd[nu - 1] = tbuf(Pn * Pn);
+        run2(ST_SQUEEZE,
+             G(modes({{Dn, Dn * KD * KD, Dn * Dn * Dn}, {Dn, KD * KD, Dn}}),
+               modes({{Dn, Dn * KD * KD, Dn * Dn}, {Dn, KD * KD, 1}}), modes({{KD * KD, 1, 1}})),
+             t2.d(), tp(t2d), ll.d(), tp(lld), rhoR[nu - 1].d(), tp(rhoRd[nu - 1]));
       }
     }
     // oblique projectors: C = R_L R_R^T = U S V^T, M = R_R^T V_k S^-1/2, N = S^-1/2 U_k^T R_L
     for (int nu = 1; nu <= d - 1; ++nu) {
       const int64_t Dn = D[nu], Pn = Dn * Dn;
-      DMat RtL, RtR;
-      factor(rhoL[nu - 1].d(), Pn, KIND_SQ_LEFT + nu - 1, RtL);
-      factor(rhoR[nu - 1].d(), Pn, KIND_SQ_RIGHT + nu - 1, RtR);
+      DMat RtL, RtR, RtLd, RtRd;
+      factor(rhoL[nu - 1].d(), Pn, KIND_SQ_LEFT + nu - 1, RtL, tp(rhoLd[nu - 1]), &RtLd);
+      factor(rhoR[nu - 1].d(), Pn, KIND_SQ_RIGHT + nu - 1, RtR, tp(rhoRd[nu - 1]), &RtRd);
       const int64_t kL = RtL.cols, kR = RtR.cols;
       DevBuf C(kL * kR * sizeof(double), st);
       eng.mm(kL, kR, Pn, RtL.p(), kL, true, RtR.p(), kR, false, C.d(), kR);
@@ -676,12 +917,9 @@ void tatrg_ctx::rg_step() {
       const int64_t k = multiplet_cut(cs.s, keep_count(cs.s, 1e-12, chi()), tau);
       TATRG_CHECK(k >= 1, TATRG_ENUMERIC, "squeezer core is zero");
       spec_sq[nu - 1] = cs.s;
-      DevBuf isq(k * sizeof(double), st);
-      {
-        std::vector<double> v(cs.s.begin(), cs.s.begin() + k);
-        for (auto& x : v) x = 1.0 / std::sqrt(x);
-        TATRG_CUDA(cudaMemcpyAsync(isq.d(), v.data(), k * sizeof(double), cudaMemcpyHostToDevice, st));
-      }
+      std::vector<double> v(cs.s.begin(), cs.s.begin() + k);
+      for (auto& x : v) x = 1.0 / std::sqrt(x);
+      DevBuf isq = eng.upload(v);
       Ms[nu - 1].buf = dalloc(Pn * k, st);
       Ms[nu - 1].rows = Pn;
       Ms[nu - 1].cols = k;
@@ -690,9 +928,36 @@ void tatrg_ctx::rg_step() {
       Nts[nu - 1].cols = k;
       eng.mm(Pn, k, kR, RtR.p(), kR, false, cs.V.p(), cs.V.cols, false, Ms[nu - 1].p(), k);
       eng.mm(Pn, k, kL, RtL.p(), kL, false, cs.U.p(), cs.U.cols, false, Nts[nu - 1].p(), k);
-      scale_axis(Ms[nu - 1].p(), isq.d(), Pn, k, 1, 1, st);
-      scale_axis(Nts[nu - 1].p(), isq.d(), Pn, k, 1, 1, st);
-      canonical_cols(Ms[nu - 1].p(), Pn, int(k), cs.s, Nts[nu - 1].p(), Pn, false);
+      if (T) {
+        // dC = dR_L^T R_R + R_L^T dR_R;  d(s^-1/2) = -s^-3/2 ds / 2
+        DevBuf Cd(kL * kR * sizeof(double), st);
+        eng.mm(kL, kR, Pn, RtLd.p(), kL, true, RtR.p(), kR, false, Cd.d(), kR);
+        eng.mm(kL, kR, Pn, RtL.p(), kL, true, RtRd.p(), kR, false, Cd.d(), kR, 1.0, 1.0);
+        Engine::SvdTan ct = eng.svd_tan(Cd.d(), kL, kR, cs, int(k), multiplet_groups(cs.s, tau));
+        std::vector<double> dv(k);
+        for (int64_t i = 0; i < k; ++i) dv[i] = -0.5 * ct.s[i] * v[i] * v[i] * v[i];
+        DevBuf isqd = eng.upload(dv);
+        for (int side = 0; side < 2; ++side) {
+          DMat& out = side == 0 ? Ms[nu - 1] : Nts[nu - 1];
+          DMat& outd = side == 0 ? Msd[nu - 1] : Ntsd[nu - 1];
+          const DMat& R = side == 0 ? RtR : RtL;
+          const DMat& Rd = side == 0 ? RtRd : RtLd;
+          const DMat& W = side == 0 ? cs.V : cs.U;
+          const DMat& Wd = side == 0 ? ct.V : ct.U;
+          const int64_t kk = side == 0 ? kR : kL;
+          outd.buf = dalloc(Pn * k, st);
+          outd.rows = Pn;
+          outd.cols = k;
+          eng.mm(Pn, k, kk, Rd.p(), kk, false, W.p(), W.cols, false, outd.p(), k);
+          eng.mm(Pn, k, kk, R.p(), kk, false, Wd.p(), k, false, outd.p(), k, 1.0, 1.0);
+          scale_axis_tan(out.p(), outd.p(), isq.d(), isqd.d(), Pn, k, 1, 1, st);
+        }
+      } else {
+        scale_axis(Ms[nu - 1].p(), isq.d(), Pn, k, 1, 1, st);
+        scale_axis(Nts[nu - 1].p(), isq.d(), Pn, k, 1, 1, st);
+      }
+      canonical_cols(Ms[nu - 1].p(), Pn, int(k), cs.s, Nts[nu - 1].p(), Pn, false, tpm(Msd[nu - 1]),
+                     tpm(Ntsd[nu - 1]));
       Kn[nu - 1] = k;
       TATRG_CUDA(cudaStreamSynchronize(st));
     }
@@ -704,111 +969,135 @@ void tatrg_ctx::rg_step() {
   const int64_t Ks = Kn[d - 2];
   const int64_t Kg = g > 0 ? prod(Kn, 0, g) : 1;
   const int64_t rowsN = D0 * Kg * Ks;  // rows of Phi / Psi: (i0, k_1..k_g, k_sep)
-  DMat phi, psi;
-  auto contract_side = [&](const DevBuf& E_, const DevBuf& F_, int64_t KA_, int64_t KX_, const DMat& I_,
-                           const DMat& J_, const std::vector<DMat>& Ws, DMat& out) {
+  DMat phi, psi, phid, psid;
+  // One side of the contraction; the tangent operands (null outside tangent mode) follow
+  // their primal ones.
+  auto contract_side = [&](const DevBuf& E_, const DevBuf& Ed_, const DevBuf& F_, const DevBuf& Fd_,
+                           int64_t KA_, int64_t KX_, const DMat& I_, const DMat& Id_, const DMat& J_,
+                           const DMat& Jd_, const std::vector<DMat>& Ws, const std::vector<DMat>& Wsd,
+                           DMat& out, DMat& outd) {
     // C1: em[i0,kA,a,b,k] = sum_a' E[i0,kA,a',a] W_sep[(a',b),k]
-    DevBuf em(D0 * KA_ * Da_ * Ds * Ks * sizeof(double), st);
-    run(ST_CONTRACT,
-        G(modes({{D0 * KA_, Ds * Da_, Da_ * Ds * Ks}, {Da_, 1, Ds * Ks}}), modes({{Ds * Ks, 1, 1}}),
-          modes({{Ds, Da_, Ds * Ks}})),
-        E_.d(), Ws[d - 2].p(), em.d());
+    DevBuf em(D0 * KA_ * Da_ * Ds * Ks * sizeof(double), st), emd = tbuf(D0 * KA_ * Da_ * Ds * Ks);
+    run2(ST_CONTRACT,
+         G(modes({{D0 * KA_, Ds * Da_, Da_ * Ds * Ks}, {Da_, 1, Ds * Ks}}), modes({{Ds * Ks, 1, 1}}),
+           modes({{Ds, Da_, Ds * Ks}})),
+         E_.d(), tp(Ed_), Ws[d - 2].p(), tpm(Wsd[d - 2]), em.d(), tp(emd));
     // C2: q[i0,kA,k,kX,g] = sum_{a,b} em[i0,kA,a,b,k] F[a,kX,b,g]
-    DevBuf qf(D0 * KA_ * Ks * KX_ * Dg * sizeof(double), st);
-    run(ST_CONTRACT,
-        G(modes({{D0 * KA_, Da_ * Ds * Ks, Ks * KX_ * Dg}, {Ks, 1, KX_ * Dg}}),
-          modes({{KX_, Ds * Dg, Dg}, {Dg, 1, 1}}), modes({{Da_, Ds * Ks, KX_ * Ds * Dg}, {Ds, Ks, Dg}})),
-        em.d(), F_.d(), qf.d());
+    DevBuf qf(D0 * KA_ * Ks * KX_ * Dg * sizeof(double), st), qfd = tbuf(D0 * KA_ * Ks * KX_ * Dg);
+    run2(ST_CONTRACT,
+         G(modes({{D0 * KA_, Da_ * Ds * Ks, Ks * KX_ * Dg}, {Ks, 1, KX_ * Dg}}),
+           modes({{KX_, Ds * Dg, Dg}, {Dg, 1, 1}}), modes({{Da_, Ds * Ks, KX_ * Ds * Dg}, {Ds, Ks, Dg}})),
+         em.d(), tp(emd), F_.d(), tp(Fd_), qf.d(), tp(qfd));
     em.release();
+    emd.release();
     // C3: P[kA,kX,k_G] = sum I[a_G,kA] J[b_G,kX] prod_nu W_nu[(a_nu,b_nu),k_nu]
-    DevBuf pm(KA_ * KX_ * Kg * sizeof(double), st);
+    DevBuf pm(KA_ * KX_ * Kg * sizeof(double), st), pmd = tbuf(KA_ * KX_ * Kg);
     if (g == 0) {
       fill(pm.d(), 1, 1.0, st);
     } else if (g == 1) {
       const int64_t D1 = D[1], K1 = Kn[0];
-      DevBuf t1(KA_ * D1 * K1 * sizeof(double), st);
-      run(ST_CONTRACT, G(modes({{KA_, 1, D1 * K1}}), modes({{D1 * K1, 1, 1}}), modes({{D1, KA_, D1 * K1}})),
-          I_.p(), Ws[0].p(), t1.d());
-      run(ST_CONTRACT,
-          G(modes({{KA_, D1 * K1, KX_ * K1}, {K1, 1, 1}}), modes({{KX_, 1, K1}}), modes({{D1, K1, KX_}})),
-          t1.d(), J_.p(), pm.d());
+      DevBuf t1(KA_ * D1 * K1 * sizeof(double), st), t1d = tbuf(KA_ * D1 * K1);
+      run2(ST_CONTRACT, G(modes({{KA_, 1, D1 * K1}}), modes({{D1 * K1, 1, 1}}), modes({{D1, KA_, D1 * K1}})),
+           I_.p(), tpm(Id_), Ws[0].p(), tpm(Wsd[0]), t1.d(), tp(t1d));
+      run2(ST_CONTRACT,
+           G(modes({{KA_, D1 * K1, KX_ * K1}, {K1, 1, 1}}), modes({{KX_, 1, K1}}), modes({{D1, K1, KX_}})),
+           t1.d(), tp(t1d), J_.p(), tpm(Jd_), pm.d(), tp(pmd));
     } else {
       const int64_t D1 = D[1], D2 = D[2], K1 = Kn[0], K2 = Kn[1];
       DevBuf t1(D2 * KA_ * D1 * K1 * sizeof(double), st), t2(KA_ * D1 * K1 * D2 * K2 * sizeof(double), st);
-      run(ST_CONTRACT, G(modes({{D2 * KA_, 1, D1 * K1}}), modes({{D1 * K1, 1, 1}}), modes({{D1, D2 * KA_, D1 * K1}})),
-          I_.p(), Ws[0].p(), t1.d());
-      run(ST_CONTRACT,
-          G(modes({{KA_ * D1 * K1, 1, D2 * K2}}), modes({{D2 * K2, 1, 1}}), modes({{D2, KA_ * D1 * K1, D2 * K2}})),
-          t1.d(), Ws[1].p(), t2.d());
-      run(ST_CONTRACT,
-          G(modes({{KA_, D1 * K1 * D2 * K2, KX_ * K1 * K2}, {K1, D2 * K2, K2}, {K2, 1, 1}}),
-            modes({{KX_, 1, K1 * K2}}), modes({{D1, K1 * D2 * K2, D2 * KX_}, {D2, K2, KX_}})),
-          t2.d(), J_.p(), pm.d());
+      DevBuf t1d = tbuf(D2 * KA_ * D1 * K1), t2d = tbuf(KA_ * D1 * K1 * D2 * K2);
+      run2(ST_CONTRACT,
+           G(modes({{D2 * KA_, 1, D1 * K1}}), modes({{D1 * K1, 1, 1}}), modes({{D1, D2 * KA_, D1 * K1}})),
+           I_.p(), tpm(Id_), Ws[0].p(), tpm(Wsd[0]), t1.d(), tp(t1d));
+      run2(ST_CONTRACT,
+           G(modes({{KA_ * D1 * K1, 1, D2 * K2}}), modes({{D2 * K2, 1, 1}}), modes({{D2, KA_ * D1 * K1, D2 * K2}})),
+           t1.d(), tp(t1d), Ws[1].p(), tpm(Wsd[1]), t2.d(), tp(t2d));
+      run2(ST_CONTRACT,
+           G(modes({{KA_, D1 * K1 * D2 * K2, KX_ * K1 * K2}, {K1, D2 * K2, K2}, {K2, 1, 1}}),
+             modes({{KX_, 1, K1 * K2}}), modes({{D1, K1 * D2 * K2, D2 * KX_}, {D2, K2, KX_}})),
+           t2.d(), tp(t2d), J_.p(), tpm(Jd_), pm.d(), tp(pmd));
     }
     // C4: out[i0,k_G,k,g] = sum_{kA,kX} q[i0,kA,k,kX,g] P[kA,kX,k_G]
     out.buf = dalloc(rowsN * Dg, st);
     out.rows = rowsN;
     out.cols = Dg;
-    run(ST_CONTRACT,
-        G(modes({{D0, KA_ * Ks * KX_ * Dg, Kg * Ks * Dg}, {Ks, KX_ * Dg, Dg}, {Dg, 1, 1}}),
-          modes({{Kg, 1, Ks * Dg}}), modes({{KA_, Ks * KX_ * Dg, KX_ * Kg}, {KX_, Dg, Kg}})),
-        qf.d(), pm.d(), out.p());
+    if (T) {
+      outd.buf = dalloc(rowsN * Dg, st);
+      outd.rows = rowsN;
+      outd.cols = Dg;
+    }
+    run2(ST_CONTRACT,
+         G(modes({{D0, KA_ * Ks * KX_ * Dg, Kg * Ks * Dg}, {Ks, KX_ * Dg, Dg}, {Dg, 1, 1}}),
+           modes({{Kg, 1, Ks * Dg}}), modes({{KA_, Ks * KX_ * Dg, KX_ * Kg}, {KX_, Dg, Kg}})),
+         qf.d(), tp(qfd), pm.d(), g == 0 ? nullptr : tp(pmd), out.p(), tpm(outd));
   };
-  contract_side(E, F, KA, KX, UA, UX, Ms, phi);
+  contract_side(E, Ed, F, Fd, KA, KX, UA, UAd, UX, UXd, Ms, Msd, phi, phid);
   // Psi: the same chain with H (for E), G (for F), L, K and the transposed N's; H carries
   // the backward leg j0(n) and L the group legs of site n, so (kD, kY) take the roles of
   // (kA, kX) with the pair order (a, b) = (leg at n+1^, leg at n) kept by N^T.
   {
     // hn[j0,kD,be,a,k] = sum_b H[j0,kD,b,be] N_sep[k,(a,b)]
-    DevBuf hn(D0 * KD * Da_ * Ds * Ks * sizeof(double), st);
-    run(ST_CONTRACT,
-        G(modes({{D0 * KD, Ds * Da_, Da_ * Ds * Ks}, {Da_, 1, Ds * Ks}}), modes({{Ds, Ds * Ks, Ks}, {Ks, 1, 1}}),
-          modes({{Ds, Da_, Ks}})),
-        H.d(), Nts[d - 2].p(), hn.d());
-    DevBuf qp(D0 * KD * Ks * KY * Dg * sizeof(double), st);
-    run(ST_CONTRACT,
-        G(modes({{D0 * KD, Da_ * Ds * Ks, Ks * KY * Dg}, {Ks, 1, KY * Dg}}),
-          modes({{KY, Ds * Dg, Dg}, {Dg, 1, 1}}), modes({{Da_, Ds * Ks, KY * Ds * Dg}, {Ds, Ks, Dg}})),
-        hn.d(), Gt.d(), qp.d());
+    DevBuf hn(D0 * KD * Da_ * Ds * Ks * sizeof(double), st), hnd = tbuf(D0 * KD * Da_ * Ds * Ks);
+    run2(ST_CONTRACT,
+         G(modes({{D0 * KD, Ds * Da_, Da_ * Ds * Ks}, {Da_, 1, Ds * Ks}}), modes({{Ds, Ds * Ks, Ks}, {Ks, 1, 1}}),
+           modes({{Ds, Da_, Ks}})),
+         H.d(), tp(Hd), Nts[d - 2].p(), tpm(Ntsd[d - 2]), hn.d(), tp(hnd));
+    DevBuf qp(D0 * KD * Ks * KY * Dg * sizeof(double), st), qpd = tbuf(D0 * KD * Ks * KY * Dg);
+    run2(ST_CONTRACT,
+         G(modes({{D0 * KD, Da_ * Ds * Ks, Ks * KY * Dg}, {Ks, 1, KY * Dg}}),
+           modes({{KY, Ds * Dg, Dg}, {Dg, 1, 1}}), modes({{Da_, Ds * Ks, KY * Ds * Dg}, {Ds, Ks, Dg}})),
+         hn.d(), tp(hnd), Gt.d(), tp(Gtd), qp.d(), tp(qpd));
     hn.release();
+    hnd.release();
     // P'[kY,kD,k_G] = sum K[a_G,kY] L[b_G,kD] prod N_nu[k,(a,b)]
-    DevBuf pm(KY * KD * Kg * sizeof(double), st);
+    DevBuf pm(KY * KD * Kg * sizeof(double), st), pmd = tbuf(KY * KD * Kg);
     if (g == 0) {
       fill(pm.d(), 1, 1.0, st);
     } else if (g == 1) {
       const int64_t D1 = D[1], K1 = Kn[0];
-      DevBuf t1(KY * D1 * K1 * sizeof(double), st);
-      run(ST_CONTRACT, G(modes({{KY, 1, D1 * K1}}), modes({{D1 * K1, 1, 1}}), modes({{D1, KY, D1 * K1}})),
-          UY.p(), Nts[0].p(), t1.d());
-      run(ST_CONTRACT,
-          G(modes({{KY, D1 * K1, KD * K1}, {K1, 1, 1}}), modes({{KD, 1, K1}}), modes({{D1, K1, KD}})),
-          t1.d(), UD.p(), pm.d());
+      DevBuf t1(KY * D1 * K1 * sizeof(double), st), t1d = tbuf(KY * D1 * K1);
+      run2(ST_CONTRACT, G(modes({{KY, 1, D1 * K1}}), modes({{D1 * K1, 1, 1}}), modes({{D1, KY, D1 * K1}})),
+           UY.p(), tpm(UYd), Nts[0].p(), tpm(Ntsd[0]), t1.d(), tp(t1d));
+      run2(ST_CONTRACT,
+           G(modes({{KY, D1 * K1, KD * K1}, {K1, 1, 1}}), modes({{KD, 1, K1}}), modes({{D1, K1, KD}})),
+           t1.d(), tp(t1d), UD.p(), tpm(UDd), pm.d(), tp(pmd));
     } else {
       const int64_t D1 = D[1], D2 = D[2], K1 = Kn[0], K2 = Kn[1];
       DevBuf t1(D2 * KY * D1 * K1 * sizeof(double), st), t2(KY * D1 * K1 * D2 * K2 * sizeof(double), st);
-      run(ST_CONTRACT, G(modes({{D2 * KY, 1, D1 * K1}}), modes({{D1 * K1, 1, 1}}), modes({{D1, D2 * KY, D1 * K1}})),
-          UY.p(), Nts[0].p(), t1.d());
-      run(ST_CONTRACT,
-          G(modes({{KY * D1 * K1, 1, D2 * K2}}), modes({{D2 * K2, 1, 1}}), modes({{D2, KY * D1 * K1, D2 * K2}})),
-          t1.d(), Nts[1].p(), t2.d());
-      run(ST_CONTRACT,
-          G(modes({{KY, D1 * K1 * D2 * K2, KD * K1 * K2}, {K1, D2 * K2, K2}, {K2, 1, 1}}),
-            modes({{KD, 1, K1 * K2}}), modes({{D1, K1 * D2 * K2, D2 * KD}, {D2, K2, KD}})),
-          t2.d(), UD.p(), pm.d());
+      DevBuf t1d = tbuf(D2 * KY * D1 * K1), t2d = tbuf(KY * D1 * K1 * D2 * K2);
+      run2(ST_CONTRACT,
+           G(modes({{D2 * KY, 1, D1 * K1}}), modes({{D1 * K1, 1, 1}}), modes({{D1, D2 * KY, D1 * K1}})),
+           UY.p(), tpm(UYd), Nts[0].p(), tpm(Ntsd[0]), t1.d(), tp(t1d));
+      run2(ST_CONTRACT,
+           G(modes({{KY * D1 * K1, 1, D2 * K2}}), modes({{D2 * K2, 1, 1}}), modes({{D2, KY * D1 * K1, D2 * K2}})),
+           t1.d(), tp(t1d), Nts[1].p(), tpm(Ntsd[1]), t2.d(), tp(t2d));
+      run2(ST_CONTRACT,
+           G(modes({{KY, D1 * K1 * D2 * K2, KD * K1 * K2}, {K1, D2 * K2, K2}, {K2, 1, 1}}),
+             modes({{KD, 1, K1 * K2}}), modes({{D1, K1 * D2 * K2, D2 * KD}, {D2, K2, KD}})),
+           t2.d(), tp(t2d), UD.p(), tpm(UDd), pm.d(), tp(pmd));
     }
     // Psi[j0,k_G,k,g] = sum_{kD,kY} qp[j0,kD,k,kY,g] P'[kY,kD,k_G]
     psi.buf = dalloc(rowsN * Dg, st);
     psi.rows = rowsN;
     psi.cols = Dg;
-    run(ST_CONTRACT,
-        G(modes({{D0, KD * Ks * KY * Dg, Kg * Ks * Dg}, {Ks, KY * Dg, Dg}, {Dg, 1, 1}}),
-          modes({{Kg, 1, Ks * Dg}}), modes({{KD, Ks * KY * Dg, Kg}, {KY, Dg, KD * Kg}})),
-        qp.d(), pm.d(), psi.p());
+    if (T) {
+      psid.buf = dalloc(rowsN * Dg, st);
+      psid.rows = rowsN;
+      psid.cols = Dg;
+    }
+    run2(ST_CONTRACT,
+         G(modes({{D0, KD * Ks * KY * Dg, Kg * Ks * Dg}, {Ks, KY * Dg, Dg}, {Dg, 1, 1}}),
+           modes({{Kg, 1, Ks * Dg}}), modes({{KD, Ks * KY * Dg, Kg}, {KY, Dg, KD * Kg}})),
+         qp.d(), tp(qpd), pm.d(), g == 0 ? nullptr : tp(pmd), psi.p(), tpm(psid));
   }
   E.release();
   F.release();
   Gt.release();
   H.release();
+  Ed.release();
+  Fd.release();
+  Gtd.release();
+  Hd.release();
 
   // ============================ re-split and rotation ============================
   tm.mark(4);
@@ -816,7 +1105,7 @@ void tatrg_ctx::rg_step() {
   std::vector<int64_t> newD(d);
   newD[0] = D0;
   for (int nu = 1; nu < d; ++nu) newD[nu] = Kn[nu - 1];
-  resplit_and_rotate(phi, psi, rowsN, Dg, newD);
+  resplit_and_rotate(phi, psi, rowsN, Dg, newD, T ? &phid : nullptr, T ? &psid : nullptr);
   tm.mark(5);
   TATRG_CUDA(cudaStreamSynchronize(st));
   for (int i = 0; i < ST_N; ++i) {
@@ -837,11 +1126,25 @@ void tatrg_ctx::rg_step() {
 }
 
 void tatrg_ctx::resplit_and_rotate(DMat& phi, DMat& psi, int64_t rows, int64_t Dg,
-                                   const std::vector<int64_t>& newD) {
+                                   const std::vector<int64_t>& newD, DMat* phid, DMat* psid) {
   cudaStream_t st = stream;
+  const bool T = tan_on;
   flops[ST_RESPLIT] += 8.0 * double(rows) * double(Dg) * double(Dg);
-  OrthResult qa = eng.orth(phi.p(), rows, Dg);
-  OrthResult qb = eng.orth(psi.p(), rows, Dg);
+  OrthResult qa, qb;
+  DMat qad, qbd, rad, rbd;  // tangents of Q_Phi, Q_Psi, R_Phi, R_Psi
+  if (T) {
+    Engine::OrthT ta = eng.orth_t(phi.p(), phid->p(), rows, Dg, tau);
+    Engine::OrthT tb = eng.orth_t(psi.p(), psid->p(), rows, Dg, tau);
+    qa = std::move(ta.o);
+    qb = std::move(tb.o);
+    qad = std::move(ta.Qd);
+    qbd = std::move(tb.Qd);
+    rad = std::move(ta.Rd);
+    rbd = std::move(tb.Rd);
+  } else {
+    qa = eng.orth(phi.p(), rows, Dg);
+    qb = eng.orth(psi.p(), rows, Dg);
+  }
   const int64_t ka = qa.k, kb = qb.k;
   DevBuf Cm(ka * kb * sizeof(double), st);
   eng.mm(ka, kb, Dg, qa.R.p(), Dg, false, qb.R.p(), Dg, true, Cm.d(), kb);
@@ -857,16 +1160,48 @@ void tatrg_ctx::resplit_and_rotate(DMat& phi, DMat& psi, int64_t rows, int64_t D
   // A'[rot] = Q_Phi U_k with rows (i0, rest) written in rotated order (rest, i0)
   DevBuf An(rows * Dn * sizeof(double), st), Bn(rows * Dn * sizeof(double), st);
   flops[ST_RESPLIT] += 4.0 * double(rows) * double(ka) * double(Dn);
-  eng.gemm(G(modes({{D0, Kr * ka, Dn}, {Kr, ka, D0 * Dn}}), modes({{Dn, 1, 1}}), modes({{ka, 1, cs.U.cols}})),
-           qa.Q.p(), cs.U.p(), An.d());
+  auto ga = [&](int64_t ldu, double beta) {
+    return G(modes({{D0, Kr * ka, Dn}, {Kr, ka, D0 * Dn}}), modes({{Dn, 1, 1}}), modes({{ka, 1, ldu}}), 1.0, beta);
+  };
   // B'[a, rot] = (Q_Psi V_k)^T
-  eng.gemm(G(modes({{D0, Kr * kb, 1}, {Kr, kb, D0}}), modes({{Dn, 1, rows}}), modes({{kb, 1, cs.V.cols}})),
-           qb.Q.p(), cs.V.p(), Bn.d());
-  canonical_cols(An.d(), rows, int(Dn), cs.s, Bn.d(), rows, true);
+  auto gb = [&](int64_t ldv, double beta) {
+    return G(modes({{D0, Kr * kb, 1}, {Kr, kb, D0}}), modes({{Dn, 1, rows}}), modes({{kb, 1, ldv}}), 1.0, beta);
+  };
+  eng.gemm(ga(cs.U.cols, 0.0), qa.Q.p(), cs.U.p(), An.d());
+  eng.gemm(gb(cs.V.cols, 0.0), qb.Q.p(), cs.V.p(), Bn.d());
+  DevBuf And, Bnd;
+  std::vector<double> dsv;
+  double dc = 0.0;
+  if (T) {
+    // dC = dR_a R_b^T + R_a dR_b^T;  dA' = dQ_a U + Q_a dU;  dB' = (dQ_b V + Q_b dV)^T
+    DevBuf Cmd(ka * kb * sizeof(double), st);
+    eng.mm(ka, kb, Dg, rad.p(), Dg, false, qb.R.p(), Dg, true, Cmd.d(), kb);
+    eng.mm(ka, kb, Dg, qa.R.p(), Dg, false, rbd.p(), Dg, true, Cmd.d(), kb, 1.0, 1.0);
+    Engine::SvdTan ct = eng.svd_tan(Cmd.d(), ka, kb, cs, int(Dn), multiplet_groups(cs.s, tau));
+    And = dalloc(rows * Dn, st);
+    Bnd = dalloc(rows * Dn, st);
+    eng.gemm(ga(cs.U.cols, 0.0), qad.p(), cs.U.p(), And.d());
+    eng.gemm(ga(Dn, 1.0), qa.Q.p(), ct.U.p(), And.d());
+    eng.gemm(gb(cs.V.cols, 0.0), qbd.p(), cs.V.p(), Bnd.d());
+    eng.gemm(gb(Dn, 1.0), qb.Q.p(), ct.V.p(), Bnd.d());
+    dsv = ct.s;
+    for (int64_t i = 0; i < Dn; ++i) dc += cs.s[i] * dsv[i];
+    dc /= c;
+  }
+  canonical_cols(An.d(), rows, int(Dn), cs.s, Bn.d(), rows, true, T ? And.d() : nullptr,
+                 T ? Bnd.d() : nullptr);
   A = std::move(An);
   B = std::move(Bn);
   Da = Dn;
   s.assign(cs.s.begin(), cs.s.begin() + Dn);
+  if (T) {
+    // s' = s / c:  ds' = ds / c - s dc / c^2;  d ln c = dc / c
+    Ad = std::move(And);
+    Bd = std::move(Bnd);
+    sd.assign(Dn, 0.0);
+    for (int64_t i = 0; i < Dn; ++i) sd[i] = dsv[i] / c - s[i] * dc / (c * c);
+    lnc_d.push_back(dc / c);
+  }
   for (auto& x : s) x /= c;
   spec_s = s;
   upload_s();
@@ -957,10 +1292,44 @@ tatrg_status tatrg_lnZ(tatrg_ctx* ctx, double* out) {
   });
 }
 
-tatrg_status tatrg_grad(tatrg_ctx* ctx, double*, double*, double*) {
-  if (!ctx) return TATRG_EINVAL;
-  ctx->err = "tatrg_grad: adjoint kernels are not built in this version";
-  return TATRG_ENOTIMPL;
+tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh, double* d2lnZ_dbeta2) {
+  if (!ctx || (!dlnZ_dbeta && !dlnZ_dh && !d2lnZ_dbeta2)) return TATRG_EINVAL;
+  return guard(ctx, [&] {
+    TATRG_CHECK(ctx->ready && ctx->ising, TATRG_ESTATE, "tatrg_grad needs a run started by tatrg_init_ising");
+    // One FP64 tangent pass per derivative: the same run (parameters, replica, number of
+    // steps) with the tangent of every tensor carried beside it.
+    auto tangent = [&](double beta, int dir) {
+      tatrg_params pp = ctx->p;
+      pp.precision = TATRG_FP64;
+      tatrg_ctx sub(pp, ctx->stream);
+      sub.replica = ctx->replica;
+      sub.tan_on = true;
+      sub.tan_dir = dir;
+      sub.init_ising(beta, ctx->h0, ctx->d);
+      for (int k = 0; k < ctx->step; ++k) sub.rg_step();
+      const double tt = sub.trace();
+      TATRG_CHECK(tt > 0.0 && std::isfinite(tt), TATRG_ENUMERIC, "non-positive final trace");
+      double sum = 0.0, comp = 0.0;  // compensated sum of 2^-k d ln c_k
+      for (size_t k = 0; k < sub.lnc_d.size(); ++k) {
+        const double y = std::ldexp(sub.lnc_d[k], -int(k)) - comp;
+        const double t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+      }
+      return sum + std::ldexp(sub.trace_tan(tt), -sub.step);
+    };
+    if (dlnZ_dbeta) *dlnZ_dbeta = tangent(ctx->beta0, 0);
+    if (dlnZ_dh) *dlnZ_dh = tangent(ctx->beta0, 1);
+    if (d2lnZ_dbeta2) {
+      // central difference of the exact first derivative; the computed ln Z / V is only
+      // piecewise smooth (ordered bases change where singular values of different
+      // symmetry sectors cross), so the step stays small
+      const double e = 1e-6 * std::max(1.0, ctx->beta0);
+      TATRG_CHECK(ctx->beta0 - e > 0.0, TATRG_EINVAL, "tatrg_grad: beta too small for the second derivative");
+      *d2lnZ_dbeta2 = (tangent(ctx->beta0 + e, 0) - tangent(ctx->beta0 - e, 0)) / (2.0 * e);
+    }
+    TATRG_CHECK(tc_error_flag(true) == 0, TATRG_ETIMEOUT, "a tensor-core pipeline wait timed out");
+  });
 }
 
 tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double h, int d,
@@ -1070,6 +1439,7 @@ tatrg_status tatrg_set_state(tatrg_ctx* ctx, int d, const int* dims, const doubl
     ctx->lnc.assign(step + 1, 0.0);
     ctx->lnc[0] = partial_lnz;
     ctx->ready = true;
+    ctx->ising = false;
     TATRG_CUDA(cudaStreamSynchronize(ctx->stream));
   });
 }

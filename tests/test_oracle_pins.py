@@ -330,3 +330,43 @@ def test_multiplet_cut_never_splits():
     assert rla.multiplet_cut(vals, 6, 1e-10) == 6
     assert rla.multiplet_cut(np.array([1.0, 1.0, 0.5]), 1, 1e-10) == 2
     assert rla.multiplets(vals, 1e-10) == [(2, 5)]
+
+
+# ---- derivatives of ln Z / V (oracle.derivatives) -------------------------------------
+
+def test_derivatives_match_enumeration_2d_torus():
+    """Untruncated 4x4 torus: the oracle's dlnZ/dbeta and dlnZ/dh equal the enumerated
+    <sum of bonds> / V and <sum of spins> / V."""
+    from oracle import derivatives
+    beta, h = 0.44, 0.07
+    _, bonds, mag = exact_ising.brute_force_lnz(beta, h, (4, 4))
+    gb = derivatives.dlnz_dbeta(beta, h, 2, INF, 4)
+    gh = derivatives.dlnz_dh(beta, h, 2, INF, 4)
+    assert abs(gb - bonds / 16) < 1e-9, (gb, bonds / 16)
+    assert abs(gh - mag / 16) < 1e-9, (gh, mag / 16)
+
+
+def test_derivative_high_temperature_series_4d():
+    """d/dbeta of ln 2 + 4 ln cosh b + 6 tanh^4 b is 4 tanh b + 24 tanh^3 b sech^2 b; at
+    beta = 0.015 the second term is 8e-5.  The chi truncation error of the derivative
+    (1.2e-5 at chi = 12) shrinks with chi; a wrong plaquette count (4e-5 per missing
+    plaquette pair) or ln cosh coefficient fails the bound."""
+    from oracle import derivatives
+    beta = 0.015
+    t = math.tanh(beta)
+    series = 4 * t + 24 * t ** 3 * (1 - t * t)
+    errs = [abs(derivatives.dlnz_dbeta(beta, 0.0, 4, trg.Params(chi, 2, q=2, seed=3), 16) - series)
+            for chi in (4, 12)]
+    assert errs[1] < 2e-5, errs
+    assert errs[1] < errs[0], errs
+
+
+def test_derivative_onsager_2d():
+    """d = 2 at chi = 16 on a 2^20 x 2^20 torus: dlnZ/dbeta approaches the derivative of
+    Onsager's free energy (taken here by a central difference of the closed form)."""
+    from oracle import derivatives
+    beta = 0.3
+    e = 1e-4
+    exact = (exact_ising.onsager_lnz(beta + e) - exact_ising.onsager_lnz(beta - e)) / (2 * e)
+    got = derivatives.dlnz_dbeta(beta, 0.0, 2, trg.Params(16, 3, q=2, seed=7), 40)
+    assert abs(got - exact) < 1e-6, (got, exact)
