@@ -218,11 +218,12 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "fp64": tg.FP64}[args.precision]
     seed = SEED + 1000 * rank
-    ctx = tg.Context(CHI, R, Q, seed=seed, precision=prec, profile=1, stream=stream)
+    chi, r = args.chi, args.r
+    ctx = tg.Context(chi, r, Q, seed=seed, precision=prec, profile=1, stream=stream)
     ctx.init_ising(BETA, H, 4)
     while True:  # setup: grow every leg to chi
         ctx.rg_step()
-        if all(x == CHI for x in list(ctx.step_info().dims)[:5]):
+        if all(x == chi for x in list(ctx.step_info().dims)[:5]):
             break
     for _ in range(args.warmup):
         ctx.rg_step()
@@ -287,7 +288,7 @@ def run_ours(args, world, rank, local):
 
     fp64_ms = None
     if args.fp64_steps > 0 and prec != tg.FP64:
-        f64 = tg.Context(CHI, R, Q, seed=seed, stream=stream)
+        f64 = tg.Context(chi, r, Q, seed=seed, stream=stream)
         f64.set_state(A, s, B, k0, 0.0)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -300,12 +301,14 @@ def run_ours(args, world, rank, local):
 
     if rank != 0:
         return
+    workload = WORKLOAD if (chi, r) == (CHI, R) else WORKLOAD.replace(
+        "chi=48 r=3", "chi=%d r=%d" % (chi, r)).replace("legs 48^4, bond 48", "legs %d^4, bond %d" % (chi, chi))
     line = {
         "metric": "RG steps/s at chi=48 (split precision); TFLOP/s; df vs FP64 oracle",
         "value": value, "unit": "RG steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "chi": CHI, "r": R, "q": Q, "precision": args.precision,
+        "config": {"workload": workload, "chi": chi, "r": r, "q": Q, "precision": args.precision,
                    "l2": "inputs larger than L2 (each step streams > 10 GB of tensors)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "tflops_algorithmic": alg_flops / (ms / 1e3) / 1e12,
@@ -341,6 +344,9 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-delta-f", action="store_true")
+    ap.add_argument("--chi", type=int, default=CHI,
+                    help="bond dimension (48 is the benchmark; smaller values size ncu captures)")
+    ap.add_argument("--r", type=int, default=R)
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
