@@ -220,13 +220,17 @@ __host__ __device__ inline void mode_offsets(const DevModes& d, int64_t flat, in
                                              int64_t& o1) {
   o0 = 0;
   o1 = 0;
-  for (int i = d.n - 1; i >= 0; --i) {
-    int64_t e = d.ext[i];
-    int64_t q = flat / e;
-    int64_t r = flat - q * e;
-    o0 += r * d.s0[i];
-    o1 += r * d.s1[i];
-    flat = q;
+#pragma unroll
+  for (int j = 0; j < kMaxModes; ++j) {  // innermost mode first; static indices (no local copy)
+    const int i = kMaxModes - 1 - j;
+    if (i < d.n) {
+      const int64_t e = d.ext[i];
+      const int64_t q = flat / e;
+      const int64_t r = flat - q * e;
+      o0 += r * d.s0[i];
+      o1 += r * d.s1[i];
+      flat = q;
+    }
   }
 }
 

@@ -43,8 +43,10 @@ struct Stats {
 // kernels_f64.cu ----------------------------------------------------------------------
 void gemm_f64(const GemmDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
               Stats* st);
+// Philox4x32-10 Gaussians; float_math evaluates Box-Muller in float (split-precision
+// sketches), otherwise in double.  out must be 16-byte aligned with float_math.
 void gaussian(uint64_t seed, uint32_t sid, uint32_t replica, int64_t n, double* out,
-              cudaStream_t s);
+              cudaStream_t s, bool float_math = false);
 // x viewed as [outer, n, inner] is multiplied along n by v^power (power 1, 2, -1, -2=rsqrt)
 void scale_axis(double* x, const double* v, int64_t outer, int64_t n, int64_t inner, int power,
                 cudaStream_t s);

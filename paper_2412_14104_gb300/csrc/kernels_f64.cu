@@ -301,16 +301,51 @@ __global__ void gaussian_kernel(uint64_t seed, uint32_t sid, uint32_t replica, i
     if (2 * p + 1 < n) out[2 * p + 1] = rad * sin(ang);
   }
 }
+
+// The same stream with Box-Muller evaluated in float arithmetic (relative error ~1e-7),
+// for sketches that feed split-precision contractions, where the operand is rounded to
+// two tensor-core numbers (~2^-22 relative) anyway.  The uniforms are the same 53-bit
+// values, rounded to float (never to zero: the smallest is 2^-54).
+__global__ void gaussian_f32_kernel(uint64_t seed, uint32_t sid, uint32_t replica, int64_t n,
+                                    double* out) {
+  const int64_t npairs = (n + 1) / 2;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npairs;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t c0 = uint32_t(p), c1 = uint32_t(uint64_t(p) >> 32), c2 = replica,
+             c3 = uint32_t(seed >> 32);
+    uint32_t k0 = uint32_t(seed), k1 = sid;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+      philox_round(c0, c1, c2, c3, k0, k1);
+    }
+    const float u1 = float(u53(c0, c1)), u2 = float(u53(c2, c3));
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);  // angle 2 pi u2, reduced exactly in units of pi
+    if (2 * p + 1 < n) {
+      reinterpret_cast<double2*>(out)[p] = make_double2(double(rad * cs), double(rad * sn));
+    } else {
+      out[2 * p] = double(rad * cs);
+    }
+  }
+}
 }  // namespace
 
 void gaussian(uint64_t seed, uint32_t sid, uint32_t replica, int64_t n, double* out,
-              cudaStream_t s) {
+              cudaStream_t s, bool float_math) {
   if (n <= 0) return;
   TATRG_CHECK(out != nullptr, TATRG_EINVAL, "gaussian: null output");
   check_extent(out, n - 1, sizeof(double), "gaussian");
   int64_t npairs = (n + 1) / 2;
   int blocks = int(std::min<int64_t>(cdiv(npairs, 256), 152 * 32));
-  gaussian_kernel<<<blocks, 256, 0, s>>>(seed, sid, replica, n, out);
+  if (float_math) {
+    TATRG_CHECK((reinterpret_cast<uintptr_t>(out) & 15) == 0, TATRG_EINVAL,
+                "gaussian: output must be 16-byte aligned");
+    gaussian_f32_kernel<<<blocks, 256, 0, s>>>(seed, sid, replica, n, out);
+  } else {
+    gaussian_kernel<<<blocks, 256, 0, s>>>(seed, sid, replica, n, out);
+  }
   TATRG_CUDA(cudaGetLastError());
 }
 

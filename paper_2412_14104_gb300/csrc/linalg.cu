@@ -9,52 +9,59 @@
 namespace tatrg {
 namespace {
 
-// Packed upper-triangular index of (i, k), k >= i.
-__device__ __forceinline__ int tri_idx(int i, int k, int n) { return i * n - (i * (i - 1)) / 2 + (k - i); }
-
-// Right-looking Cholesky G + shift I = R^T R with the upper triangle held packed in shared
-// memory (n <= 160); R is written row-major with zeros below the diagonal.
+// Right-looking Cholesky G + shift I = R^T R with the upper triangle of the working
+// matrix in shared memory (full n x n storage, n <= 160).  Step j: every thread takes
+// the pivot square root itself, row j is scaled into R's row j (and a shared copy), then
+// the trailing block subtracts the outer product of the scaled row: two block barriers per
+// step.  A pivot at or below 1e-14 of its original diagonal entry is a breakdown
+// (status 1).
 __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, double* R,
                                                         int* status, double shift_rel) {
   extern __shared__ double W[];
-  __shared__ int fail;
   __shared__ double shift;
+  __shared__ double red[32];
+  __shared__ double rowj[160];
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) {
-    fail = 0;
+  const int tx = tid & 31, ty = tid >> 5;  // 32 x 32 threads over (k, i)
+  {
     double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += G[int64_t(i) * n + i];
-    shift = shift_rel * tr;
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, k = e % n;
-    if (k >= i) W[tri_idx(i, k, n)] = G[e] + (i == k ? shift : 0.0);
-  }
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
+    for (int i = tid; i < n; i += nt) tr += G[int64_t(i) * n + i];
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+    if (tx == 0) red[ty] = tr;
+    __syncthreads();
     if (tid == 0) {
-      double d = W[tri_idx(j, j, n)];
-      double ref = G[int64_t(j) * n + j] + shift;
-      if (!(d > 1e-14 * ref) || !(ref > 0.0)) fail = 1;
-      else W[tri_idx(j, j, n)] = sqrt(d);
-    }
-    __syncthreads();
-    if (fail) break;
-    const double djj = W[tri_idx(j, j, n)];
-    for (int k = j + 1 + tid; k < n; k += nt) W[tri_idx(j, k, n)] /= djj;
-    __syncthreads();
-    const int rem = n - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      int i = j + 1 + e / rem, k = j + 1 + e % rem;
-      if (k >= i) W[tri_idx(i, k, n)] -= W[tri_idx(j, i, n)] * W[tri_idx(j, k, n)];
+      double t = 0.0;
+      for (int w = 0; w < (nt >> 5); ++w) t += red[w];
+      shift = shift_rel * t;
     }
     __syncthreads();
   }
+  const double sh = shift;
   for (int e = tid; e < n * n; e += nt) {
-    int i = e / n, k = e % n;
-    R[e] = (k >= i && !fail) ? W[tri_idx(i, k, n)] : 0.0;
+    const int i = e / n, k = e - (e / n) * n;
+    W[e] = (k >= i) ? G[e] + (i == k ? sh : 0.0) : 0.0;
   }
+  int fail = 0;
+  for (int j = 0; j < n; ++j) {
+    __syncthreads();
+    const double d = W[j * n + j];
+    const double ref = G[int64_t(j) * n + j] + sh;
+    if (!(d > 1e-14 * ref) || !(ref > 0.0)) { fail = 1; break; }  // uniform across the block
+    const double djj = sqrt(d);
+    for (int k = j + tid; k < n; k += nt) {
+      const double x = (k == j) ? djj : W[j * n + k] / djj;
+      rowj[k] = x;
+      W[j * n + k] = x;
+    }
+    __syncthreads();
+    for (int i = j + 1 + ty; i < n; i += 32) {
+      const double a = rowj[i];
+      for (int k = i + ((tx - (i - (j + 1))) & 31); k < n; k += 32)
+        W[i * n + k] = fma(-a, rowj[k], W[i * n + k]);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nt) R[e] = fail ? 0.0 : W[e];
   if (tid == 0) *status = fail;
 }
 
@@ -429,9 +436,9 @@ void cholesky(const double* G, int n, double* R, int* status_dev, double shift_r
   check_extent(G, int64_t(n) * n - 1, sizeof(double), "cholesky input");
   check_extent(R, int64_t(n) * n - 1, sizeof(double), "cholesky output");
   TATRG_CHECK(n >= 1 && n <= 160, TATRG_EINVAL, "cholesky: n must be <= 160");
-  const size_t sm = size_t(n) * (n + 1) / 2 * sizeof(double);
+  const size_t sm = size_t(n) * n * sizeof(double);
   static const cudaError_t attr = cudaFuncSetAttribute(  // once, thread-safe
-      cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 161 / 2 * 8);
+      cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 160 * 8);
   TATRG_CUDA(attr);
   cholesky_kernel<<<1, 1024, sm, s>>>(G, n, R, status_dev, shift_rel);
   TATRG_CUDA(cudaGetLastError());

@@ -327,7 +327,7 @@ DMat tatrg_ctx::isometry(const double* rho, int64_t Gd, int kind, std::vector<do
     if (rhod) et = eng.svd_tan(rhod, Gd, Gd, e, keep_count(e.s, 1e-14, k), multiplet_groups(e.s, tau));
   } else {
     DevBuf om(Gd * k * sizeof(double), stream);
-    gaussian(p.seed, stream_id(step, kind), replica, Gd * k, om.d(), stream);
+    gaussian(p.seed, stream_id(step, kind), replica, Gd * k, om.d(), stream, eng.prec != 0);
     if (rhod) {
       Engine::RsvdT r = eng.rsvd_psd_t(rho, rhod, Gd, k, p.q, om.d(), tau);
       e = std::move(r.e);
@@ -365,7 +365,7 @@ void tatrg_ctx::factor(const double* rho, int64_t P, int kind, DMat& Rt, const d
     if (rhod) et = eng.svd_tan(rhod, P, P, e, keep_count(e.s, 1e-14, ell), multiplet_groups(e.s, tau));
   } else {
     DevBuf om(P * ell * sizeof(double), stream);
-    gaussian(p.seed, stream_id(step, kind), replica, P * ell, om.d(), stream);
+    gaussian(p.seed, stream_id(step, kind), replica, P * ell, om.d(), stream, eng.prec != 0);
     if (rhod) {
       Engine::RsvdT r = eng.rsvd_psd_t(rho, rhod, P, ell, p.q, om.d(), tau);
       e = std::move(r.e);
@@ -499,7 +499,7 @@ void tatrg_ctx::rg_step() {
     if (T) swt = eng.svd_tan(midd.d(), rows, rows, sw, keep_count(sw.s, 1e-14, sw.r), multiplet_groups(sw.s, tau));
   } else {
     DevBuf om(rows * ell * sizeof(double), st);
-    gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st);
+    gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st, eng.prec != 0);
     // M X: W[a,k,b,p] = sum_j Bs[a,k,j] X[(b,j),p];  Y[(a,i),p] = sum_{k,b} As[k,i,b] W[a,k,b,p]
     // (with any pair of factors Ap, Bp in place of As, Bs; beta = 1 accumulates into Y)
     auto apply_g = [&](const double* Ap, const double* Bp, const double* X, int64_t w, double* Y,
@@ -626,7 +626,7 @@ void tatrg_ctx::rg_step() {
     if (!done) {
       if (om.empty()) {
         om = DevBuf(rows * ell * sizeof(double), st);
-        gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st);
+        gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st, eng.prec != 0);
       }
       if (T) {
         Engine::RsvdT r = eng.rsvd_t(apply, rapply, apply_d, rapply_d, rows, rows, ell, p.q, om.d(), tau);

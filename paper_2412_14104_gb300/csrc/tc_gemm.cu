@@ -119,6 +119,37 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_u32(bar))
       : "memory");
 }
+// 16 columns of 32 lanes; the caller waits with tmem_wait_ld before using r
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
@@ -147,25 +178,89 @@ struct TcArgs {
   DevModes nC;  // s1 = C stride of each N mode
   int64_t M, N;
   int kb_per_split, nkb;
-  int mtiles, ntiles;  // output tiles; blockIdx.x walks them in groups of GROUP_M rows
+  int mtiles, ntiles;  // output tiles, walked in groups of GROUP_M row panels
+  int split;           // K ranges per tile; work unit u = split index * tiles + tile
   double alpha, beta;
   int atomic;
   double* C;
 };
 
-// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+// Packed pairs of floats (sm_100+ f32x2 arithmetic, round to nearest in each lane).
+__device__ __forceinline__ uint64_t pk(uint32_t lo, uint32_t hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpk(uint64_t x, uint32_t& lo, uint32_t& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(x));
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+// (hi, lo) += v for two lanes at once: Knuth's TwoSum of hi and v, its error added to lo.
+__device__ __forceinline__ void two_sum_acc2(uint64_t& hi, uint64_t& lo, uint64_t v) {
+  const uint64_t s = add2(hi, v);
+  const uint64_t bb = sub2(s, hi);
+  const uint64_t e = add2(sub2(hi, sub2(s, bb)), sub2(v, bb));
+  lo = add2(lo, e);
+  hi = s;
 }
 
-// 128 x 128 output tile.  The K loop is cut into chunks of KC stages; each chunk
-// accumulates in one of two TMEM buffers (columns [0,128) and [128,256)) while the eight
-// epilogue warps drain the other one into per-thread double-float (hi, lo) sums, so no FP32
-// accumulation chain in the tensor memory is longer than KC * 64 bytes of K.
-template <int PREC, int KC, int STAGES>
-__global__ void __launch_bounds__(320, 1)
+// Output tile of work unit u: grouped raster (GROUP_M consecutive row panels sweep all
+// column panels together, so the CTAs working at one time share a few A and B panels
+// that stay in L2) and the K range of its split index.
+struct Unit {
+  int64_t m0, n0;
+  int kb0, nk;
+};
+__device__ __forceinline__ Unit unit_of(const TcArgs& g, int u) {
+  constexpr int GROUP_M = 8;
+  const int tiles = g.mtiles * g.ntiles;
+  const int sidx = u / tiles, b = u - sidx * tiles;
+  const int per_group = GROUP_M * g.ntiles;
+  const int first = (b / per_group) * GROUP_M;
+  const int gsize = min(g.mtiles - first, GROUP_M);
+  const int mt = first + (b % per_group) % gsize;
+  const int nt = (b % per_group) / gsize;
+  Unit w;
+  w.m0 = int64_t(mt) * TC_BM;
+  w.n0 = int64_t(nt) * TC_BN;
+  w.kb0 = sidx * g.kb_per_split;
+  w.nk = min(g.nkb, w.kb0 + g.kb_per_split) - w.kb0;
+  return w;
+}
+
+// Persistent kernel: CTA b processes work units b, b + gridDim.x, ...; each unit is a
+// 128 x 128 output tile over one K range.  The K loop is cut into chunks of KC stages;
+// each chunk accumulates in one of NBUF TMEM buffers of 128 columns while the sixteen
+// epilogue warps drain finished ones into per-thread double-float (hi, lo) sums, so no FP32
+// accumulation chain in the tensor memory is longer than KC * 64 bytes of K.  The shared
+// memory ring, the TMEM buffers and their barriers run on across units, so the loads and
+// MMAs of the next unit overlap the drain and the stores of the current one.
+constexpr int EPI_WARPS = 16;
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;
+
+// AND of p over the epilogue warps (named barrier 1); every epilogue thread must call it.
+__device__ __forceinline__ bool epilogue_all(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.and.pred b, 1, %2, a;\n"
+      " selp.u32 %0, 1, 0, b;\n}\n"
+      : "=r"(r)
+      : "r"(uint32_t(p)), "r"(EPI_WARPS * 32)
+      : "memory");
+  return r != 0;
+}
+
+template <int PREC, int KC, int STAGES, int NBUF>
+__global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's register file
     tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                    const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
                    TcArgs g) {
@@ -174,40 +269,25 @@ __global__ void __launch_bounds__(320, 1)
   constexpr int B_TILE = BN * KSLICE;
   constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;
   constexpr int KELEM = PREC == 1 ? KSLICE / 4 : KSLICE / 2;  // K elements per stage
+  constexpr int TMEM_COLS = NBUF * BN + 2 * BN;  // chunk buffers, running hi, running lo
+  static_assert(TMEM_COLS == 512, "the tensor memory holds exactly 512 columns");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[2], acc_empty[2], fin_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[NBUF], acc_empty[NBUF], fin_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int64_t col_off[BN];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // grouped raster: GROUP_M consecutive row panels sweep all column panels together, so
-  // the CTAs resident at one time share a few A and B panels that stay in L2
-  int mt, nt;
-  {
-    constexpr int GROUP_M = 8;
-    const int b = blockIdx.x;
-    const int per_group = GROUP_M * g.ntiles;
-    const int first = (b / per_group) * GROUP_M;
-    const int gsize = min(g.mtiles - first, GROUP_M);
-    mt = first + (b % per_group) % gsize;
-    nt = (b % per_group) / gsize;
-  }
-  const int64_t m0 = int64_t(mt) * TC_BM, n0 = int64_t(nt) * BN;
-  const int kb0 = blockIdx.y * g.kb_per_split;
-  const int kb1 = min(g.nkb, kb0 + g.kb_per_split);
-  const int nk = kb1 - kb0;
-  const int nchunks = (nk + KC - 1) / KC;
-  const uint64_t deadline = now_ns() + WAIT_NS * 4;  // whole-CTA bound
+  const int units = g.mtiles * g.ntiles * g.split;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 8);
+      mbar_init(&acc_empty[b], EPI_WARPS);
     }
     mbar_init(&fin_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -216,15 +296,8 @@ __global__ void __launch_bounds__(320, 1)
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_base_s)),
-                 "r"(uint32_t(2 * BN)));
+                 "r"(uint32_t(TMEM_COLS)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (warp >= 2) {  // per-column C offsets of this tile
-    for (int j = threadIdx.x - 64; j < BN; j += 256) {
-      int64_t a = 0, c = 0;
-      if (n0 + j < g.N) mode_offsets(g.nC, n0 + j, a, c);
-      col_off[j] = c;
-    }
   }
   tc_fence_before();
   __syncthreads();
@@ -232,101 +305,156 @@ __global__ void __launch_bounds__(320, 1)
   const uint32_t tmem = tmem_base_s;
 
   if (warp == 0) {
-    if (lane == 0 && nk > 0) {
-      int issued = 0;
-      for (int i = 0; i < nk; ++i) {
-        const int s = i % STAGES, round = i / STAGES;
-        if (round > 0 && !mbar_wait(&empty_bar[s], (round - 1) & 1, deadline)) break;
-        uint8_t* st = smem + s * STAGE;
-        mbar_expect_tx(&full_bar[s], STAGE);
-        const int kx = (kb0 + i) * KELEM;
-        tma_load_2d(st, &ta_hi, &full_bar[s], kx, int(m0));
-        tma_load_2d(st + A_TILE, &ta_lo, &full_bar[s], kx, int(m0));
-        tma_load_2d(st + 2 * A_TILE, &tb_hi, &full_bar[s], kx, int(n0));
-        tma_load_2d(st + 2 * A_TILE + B_TILE, &tb_lo, &full_bar[s], kx, int(n0));
-        issued = i + 1;
+    if (lane == 0) {
+      int it = 0;  // stage uses, continued across units
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const Unit w = unit_of(g, u);
+        for (int i = 0; i < w.nk; ++i, ++it) {
+          const int s = it % STAGES, round = it / STAGES;
+          if (round > 0 && !mbar_wait(&empty_bar[s], (round - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+          uint8_t* st = smem + s * STAGE;
+          mbar_expect_tx(&full_bar[s], STAGE);
+          const int kx = (w.kb0 + i) * KELEM;
+          tma_load_2d(st, &ta_hi, &full_bar[s], kx, int(w.m0));
+          tma_load_2d(st + A_TILE, &ta_lo, &full_bar[s], kx, int(w.m0));
+          tma_load_2d(st + 2 * A_TILE, &tb_hi, &full_bar[s], kx, int(w.n0));
+          tma_load_2d(st + 2 * A_TILE + B_TILE, &tb_lo, &full_bar[s], kx, int(w.n0));
+        }
       }
       // drain: the last loads issued into each stage must have landed before the CTA exits
       const uint64_t drain = now_ns() + WAIT_NS;
-      for (int i = max(0, issued - STAGES); i < issued; ++i)
+      for (int i = max(0, it - STAGES); i < it; ++i)
         mbar_wait(&full_bar[i % STAGES], (i / STAGES) & 1, drain);
     }
   } else if (warp == 1) {
-    if (lane == 0 && nk > 0) {
+    if (lane == 0) {
       constexpr uint32_t id = idesc<PREC, BN>();
+      int it = 0, cc = 0;  // stage uses and chunks, continued across units
       bool ok = true;
-      for (int c = 0; c < nchunks && ok; ++c) {
-        const int b = c & 1, use = c >> 1;
-        if (use > 0 && !mbar_wait(&acc_empty[b], (use - 1) & 1, deadline)) { ok = false; break; }
-        tc_fence_after();
-        const uint32_t acc = tmem + uint32_t(b * BN);
-        const int i_end = min(nk, (c + 1) * KC);
-        for (int i = c * KC; i < i_end; ++i) {
-          const int s = i % STAGES, round = i / STAGES;
-          if (!mbar_wait(&full_bar[s], round & 1, deadline)) { ok = false; break; }
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const Unit w = unit_of(g, u);
+        const int nchunks = (w.nk + KC - 1) / KC;
+        for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+          const int b = cc % NBUF, use = cc / NBUF;
+          if (use > 0 && !mbar_wait(&acc_empty[b], (use - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t base = smem_u32(smem + s * STAGE);
-          const uint64_t ahi = sdesc_sw64(base), alo = sdesc_sw64(base + A_TILE);
-          const uint64_t bhi = sdesc_sw64(base + 2 * A_TILE), blo = sdesc_sw64(base + 2 * A_TILE + B_TILE);
+          const uint32_t acc = tmem + uint32_t(b * BN);
+          const int i_end = min(w.nk, (c + 1) * KC);
+          for (int i = c * KC; i < i_end; ++i, ++it) {
+            const int s = it % STAGES, round = it / STAGES;
+            if (!mbar_wait(&full_bar[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * STAGE);
+            const uint64_t ahi = sdesc_sw64(base), alo = sdesc_sw64(base + A_TILE);
+            const uint64_t bhi = sdesc_sw64(base + 2 * A_TILE), blo = sdesc_sw64(base + 2 * A_TILE + B_TILE);
 #pragma unroll
-          for (int kk = 0; kk < KSLICE / 32; ++kk) {  // 32 bytes of K per instruction
-            const uint64_t off = uint64_t(kk * 2);
-            mma<PREC>(acc, alo + off, bhi + off, id, (i > c * KC || kk > 0) ? 1u : 0u);
-            mma<PREC>(acc, ahi + off, blo + off, id, 1u);
-            mma<PREC>(acc, ahi + off, bhi + off, id, 1u);
+            for (int kk = 0; kk < KSLICE / 32; ++kk) {  // 32 bytes of K per instruction
+              const uint64_t off = uint64_t(kk * 2);
+              mma<PREC>(acc, alo + off, bhi + off, id, (i > c * KC || kk > 0) ? 1u : 0u);
+              mma<PREC>(acc, ahi + off, blo + off, id, 1u);
+              mma<PREC>(acc, ahi + off, bhi + off, id, 1u);
+            }
+            mma_commit(&empty_bar[s]);
           }
-          mma_commit(&empty_bar[s]);
+          if (ok) mma_commit(&acc_full[b]);
         }
-        if (ok) mma_commit(&acc_full[b]);
       }
       // drain: every MMA issued by this thread completes before TMEM is released
       mma_commit(&fin_bar);
       mbar_wait(&fin_bar, 0, now_ns() + WAIT_NS);
     }
-  } else if (nk > 0) {
-    // epilogue warps 2..9: TMEM lane quarter q = warp % 4, column half h
+  } else {
+    // epilogue warps 2..17: TMEM lane quarter q = warp % 4 (the lanes a warp may access),
+    // column quarter h.  The running double-float sums of the tile live in TMEM columns
+    // [NBUF*BN, NBUF*BN + BN) (hi) and [NBUF*BN + BN, NBUF*BN + 2*BN) (lo), so the drain
+    // needs few registers.
     const int q = warp & 3, h = (warp - 2) >> 2;
     const int row = q * 32 + lane;
-    float hi[64], lo[64];
-#pragma unroll
-    for (int j = 0; j < 64; ++j) { hi[j] = 0.f; lo[j] = 0.f; }
+    const uint32_t lanes = tmem + (uint32_t(q * 32) << 16);
+    const uint32_t t_hi = lanes + uint32_t(NBUF * BN + h * 32);
+    const uint32_t t_lo = lanes + uint32_t(NBUF * BN + BN + h * 32);
+    int cc = 0;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const int b = c & 1, use = c >> 1;
-      ok = __all_sync(0xffffffffu, (ok && mbar_wait(&acc_full[b], use & 1, deadline)) ? 1 : 0) != 0;
-      if (!ok) break;
-      tc_fence_after();
-      const uint32_t ta = tmem + (uint32_t(q * 32) << 16) + uint32_t(b * BN + h * 64);
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        uint32_t v[32];
-        tmem_ld32(ta + uint32_t(32 * half), v);
-        if (half == 1) {  // both halves are in registers: hand the buffer back to the MMA warp
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0)
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float s, e;
-          two_sum(hi[32 * half + j], __uint_as_float(v[j]), s, e);
-          hi[32 * half + j] = s;
-          lo[32 * half + j] = __fadd_rn(lo[32 * half + j], e);
-        }
+#pragma unroll 1
+    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      const Unit w = unit_of(g, u);
+      // per-column C offsets of this tile (the previous tile's stores are done with them)
+      asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+      for (int j = threadIdx.x - 64; j < BN; j += EPI_WARPS * 32) {
+        int64_t a = 0, c = 0;
+        if (w.n0 + j < g.N) mode_offsets(g.nC, w.n0 + j, a, c);
+        col_off[j] = c;
       }
-    }
-    if (ok && (m0 + row) < g.M) {
-      int64_t roff = 0, dummy = 0;
-      mode_offsets(g.mC, m0 + row, dummy, roff);
+      asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+      const int nchunks = (w.nk + KC - 1) / KC;
+#pragma unroll 1
+      for (int c = 0; c < nchunks; ++c, ++cc) {
+        const int b = cc % NBUF, use = cc / NBUF;
+        ok = __all_sync(0xffffffffu, (ok && mbar_wait(&acc_full[b], use & 1, now_ns() + WAIT_NS)) ? 1 : 0) != 0;
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t ta = lanes + uint32_t(b * BN + h * 32);
 #pragma unroll
-      for (int j = 0; j < 64; ++j) {
-        const int col = h * 64 + j;
-        if (n0 + col < g.N) {
-          double* p = g.C + roff + col_off[col];
-          const double x = g.alpha * (double(hi[j]) + double(lo[j]));
-          if (g.atomic) atomicAdd(p, x);
-          else *p = (g.beta != 0.0) ? x + g.beta * *p : x;
+        for (int part = 0; part < 2; ++part) {
+          uint32_t v[16], vh[16], vl[16];
+          tmem_ld16_nowait(ta + uint32_t(16 * part), v);
+          if (c > 0) {
+            tmem_ld16_nowait(t_hi + uint32_t(16 * part), vh);
+            tmem_ld16_nowait(t_lo + uint32_t(16 * part), vl);
+          }
+          tmem_wait_ld();
+          if (part == 1) {  // the whole slice has been read: hand the buffer back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+          }
+          if (c == 0) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) { vh[j] = v[j]; vl[j] = 0u; }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+              uint64_t h2 = pk(vh[j], vh[j + 1]), l2 = pk(vl[j], vl[j + 1]);
+              two_sum_acc2(h2, l2, pk(v[j], v[j + 1]));
+              unpk(h2, vh[j], vh[j + 1]);
+              unpk(l2, vl[j], vl[j + 1]);
+            }
+          }
+          tmem_st16(t_hi + uint32_t(16 * part), vh);
+          tmem_st16(t_lo + uint32_t(16 * part), vl);
+        }
+        tmem_wait_st();
+      }
+      // one decision for all epilogue warps (a wait that ran out in any of them stops all)
+      ok = epilogue_all(ok);
+      if (ok) {
+        const bool in_rows = (w.m0 + row) < g.M;
+        int64_t roff = 0, dummy = 0;
+        if (in_rows) mode_offsets(g.mC, w.m0 + row, dummy, roff);
+        double* const crow = g.C + roff;
+        const int64_t rem_ = g.N - (w.n0 + h * 32);
+        const int ncols = !in_rows ? 0 : (rem_ < 32 ? int(rem_) : 32);
+        const double alpha = g.alpha, beta = g.beta;
+        const int mode = g.atomic ? 2 : (beta != 0.0 ? 1 : 0);
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          uint32_t vh[16], vl[16];
+          tmem_ld16_nowait(t_hi + uint32_t(16 * part), vh);
+          tmem_ld16_nowait(t_lo + uint32_t(16 * part), vl);
+          tmem_wait_ld();
+          const int64_t* const co = col_off + h * 32 + 16 * part;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (16 * part + j < ncols) {
+              double* p = crow + co[j];
+              const double x = alpha * (double(__uint_as_float(vh[j])) + double(__uint_as_float(vl[j])));
+              if (mode == 2) atomicAdd(p, x);
+              else if (mode == 1) *p = fma(beta, *p, x);
+              else *p = x;
+            }
+          }
         }
       }
     }
@@ -335,7 +463,7 @@ __global__ void __launch_bounds__(320, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(2 * BN)));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(TMEM_COLS)));
   }
 }
 
@@ -347,50 +475,85 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
+// One block packs a strip of PK_R rows x PK_K K-elements per iteration (grid-stride over
+// strips).  The row and K offsets of the strip are decomposed once into shared memory.
+// K-contiguous sources are read and written with the lanes along K (no staging);
+// row-contiguous sources are read with the lanes along the rows into a shared tile and
+// written from it with the lanes along K.
+constexpr int PK_R = 32, PK_K = 128;
+
+template <int PREC>
+__device__ __forceinline__ void pack_store(void* hi, void* lo, int64_t o, double x) {
+  if (PREC == 1) {
+    const float h = tf32_rna(__double2float_rn(x));
+    const float l = tf32_rna(__double2float_rn(x - double(h)));
+    reinterpret_cast<float*>(hi)[o] = h;
+    reinterpret_cast<float*>(lo)[o] = l;
+  } else {
+    const __nv_bfloat16 h = __double2bfloat16(x);
+    const __nv_bfloat16 l = __double2bfloat16(x - double(__bfloat162float(h)));
+    reinterpret_cast<__nv_bfloat16*>(hi)[o] = h;
+    reinterpret_cast<__nv_bfloat16*>(lo)[o] = l;
+  }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ src, DevModes rm,
                                                    DevModes km, int64_t R, int64_t K, int64_t Kp,
                                                    int64_t ktiles, int64_t ntiles, void* hi,
                                                    void* lo, int r_contig) {
-  __shared__ int64_t roff[32], koff[32];
-  __shared__ double tile[32][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  __shared__ int64_t roff[PK_R], koff[PK_K];
+  __shared__ double tile[PK_R][PK_K + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;  // 8 warps
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t r0 = (t / ktiles) * 32, k0 = (t % ktiles) * 32;
-    __syncthreads();
-    if (ty == 0) {
+    const int64_t r0 = (t / ktiles) * PK_R, k0 = (t % ktiles) * PK_K;
+    __syncthreads();  // the previous strip is done with roff, koff and tile
+    if (tid < PK_R) {
       int64_t a = 0, b = 0;
-      if (r0 + tx < R) mode_offsets(rm, r0 + tx, a, b);
-      roff[tx] = a;
-    } else if (ty == 1) {
+      if (r0 + tid < R) mode_offsets(rm, r0 + tid, a, b);
+      roff[tid] = a;
+    } else if (tid < PK_R + PK_K) {
+      const int j = tid - PK_R;
       int64_t a = 0, b = 0;
-      if (k0 + tx < K) mode_offsets(km, k0 + tx, a, b);
-      koff[tx] = a;
+      if (k0 + j < K) mode_offsets(km, k0 + j, a, b);
+      koff[j] = a;
     }
     __syncthreads();
-    for (int i = ty; i < 32; i += 8) {
-      // r-contiguous sources are read with the lanes along r, others along k
-      const int rr = r_contig ? tx : i, kk = r_contig ? i : tx;
-      double v = 0.0;
-      if (r0 + rr < R && k0 + kk < K) v = src[roff[rr] + koff[kk]];
-      tile[rr][kk] = v;
-    }
-    __syncthreads();
-    for (int i = ty; i < 32; i += 8) {
-      const int64_t r = r0 + i, k = k0 + tx;
-      if (k >= Kp) continue;
-      const double x = tile[i][tx];
-      const int64_t o = r * Kp + k;
-      if (PREC == 1) {
-        const float h = tf32_rna(__double2float_rn(x));
-        const float l = tf32_rna(__double2float_rn(x - double(h)));
-        reinterpret_cast<float*>(hi)[o] = h;
-        reinterpret_cast<float*>(lo)[o] = l;
-      } else {
-        const __nv_bfloat16 h = __double2bfloat16(x);
-        const __nv_bfloat16 l = __double2bfloat16(x - double(__bfloat162float(h)));
-        reinterpret_cast<__nv_bfloat16*>(hi)[o] = h;
-        reinterpret_cast<__nv_bfloat16*>(lo)[o] = l;
+    if (!r_contig) {
+      // warp w: rows w, w + 8, ...; lanes along K (coalesced reads and writes)
+#pragma unroll
+      for (int i = 0; i < PK_R / 8; ++i) {
+        const int rr = warp + 8 * i;
+        const int64_t r = r0 + rr;
+        double v[PK_K / 32];
+#pragma unroll
+        for (int j = 0; j < PK_K / 32; ++j) {
+          const int kk = lane + 32 * j;
+          v[j] = (r < R && k0 + kk < K) ? __ldg(src + roff[rr] + koff[kk]) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < PK_K / 32; ++j) {
+          const int64_t k = k0 + lane + 32 * j;
+          if (k < Kp) pack_store<PREC>(hi, lo, r * Kp + k, v[j]);
+        }
+      }
+    } else {
+      // lanes along the rows for the reads (the source is contiguous in r)
+#pragma unroll
+      for (int i = 0; i < PK_K / 8; ++i) {
+        const int kk = warp + 8 * i;
+        const bool ok = (r0 + lane < R) && (k0 + kk < K);
+        tile[lane][kk] = ok ? __ldg(src + roff[lane] + koff[kk]) : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < PK_R / 8; ++i) {
+        const int rr = warp + 8 * i;
+#pragma unroll
+        for (int j = 0; j < PK_K / 32; ++j) {
+          const int64_t k = k0 + lane + 32 * j;
+          if (k < Kp) pack_store<PREC>(hi, lo, (r0 + rr) * Kp + k, tile[rr][lane + 32 * j]);
+        }
       }
     }
   }
@@ -446,11 +609,17 @@ void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& b
   constexpr int STAGES = SMEM_BUDGET / STAGE;
   constexpr int KC = PREC == 1 ? TATRG_KC_TF32 : TATRG_KC_BF16;  // stages per FP32 chain
   constexpr int SMEM = STAGES * STAGE + 1024;
-  auto k = tc_gemm_kernel<PREC, KC, STAGES>;
+  auto k = tc_gemm_kernel<PREC, KC, STAGES, 2>;
   static const cudaError_t attr =  // once per instantiation, thread-safe
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   TATRG_CUDA(attr);
-  k<<<grid, 320, SMEM, s>>>(ahi, alo, bhi, blo, a);
+  static const int resident = [&]() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, TC_THREADS, SMEM) != cudaSuccess) n = 0;
+    return n;
+  }();
+  TATRG_CHECK(resident >= 1, TATRG_ECUDA, "gemm_tc: the tensor-core kernel does not fit on an SM");
+  k<<<grid, TC_THREADS, SMEM, s>>>(ahi, alo, bhi, blo, a);
   TATRG_CUDA(cudaGetLastError());
 }
 
@@ -499,10 +668,10 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     // A: rows = m (stride s0), k (stride s0);  B: rows = n (s0), k (s1)
     DevModes rm = dev(d.m), km = dev(d.k);
     const int rc = (d.m.n > 0 && d.m.s0[d.m.n - 1] == 1 && !(d.k.n > 0 && d.k.s0[d.k.n - 1] == 1)) ? 1 : 0;
-    const int64_t kt = cdiv(Kp, 32), ta = (Mp / 32) * kt;
-    const int ga = int(std::min<int64_t>(ta, 152 * 64));
-    if (prec == 1) pack_kernel<1><<<ga, dim3(32, 8), 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
-    else pack_kernel<2><<<ga, dim3(32, 8), 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
+    const int64_t kt = cdiv(Kp, PK_K), ta = (Mp / PK_R) * kt;
+    const int ga = int(std::min<int64_t>(ta, 152 * 6));
+    if (prec == 1) pack_kernel<1><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
+    else pack_kernel<2><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
     TATRG_CUDA(cudaGetLastError());
     // a Gram (B is A read the same way) reuses A's panels
     bool same = (A == B) && Np == Mp && d.m.n == d.n.n && d.k.n > 0;
@@ -515,11 +684,11 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     DevModes rn = dev(d.n), kn = dev(d.k);
     for (int i = 0; i < kMaxModes; ++i) kn.s0[i] = kn.s1[i];  // B's k strides
     const int rcb = (d.n.n > 0 && d.n.s0[d.n.n - 1] == 1 && !(d.k.n > 0 && d.k.s1[d.k.n - 1] == 1)) ? 1 : 0;
-    const int64_t tb = (Np / 32) * kt;
-    const int gb = int(std::min<int64_t>(tb, 152 * 64));
+    const int64_t tb = (Np / PK_R) * kt;
+    const int gb = int(std::min<int64_t>(tb, 152 * 6));
     if (!same) {
-      if (prec == 1) pack_kernel<1><<<gb, dim3(32, 8), 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
-      else pack_kernel<2><<<gb, dim3(32, 8), 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
+      if (prec == 1) pack_kernel<1><<<gb, 256, 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
+      else pack_kernel<2><<<gb, 256, 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
       TATRG_CUDA(cudaGetLastError());
     }
   }
@@ -551,9 +720,18 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   }
   a.mtiles = int(Mp / TC_BM);
   a.ntiles = int(Np / BN);
-  TATRG_CHECK(int64_t(a.mtiles) * a.ntiles < (int64_t(1) << 31) && split <= 65535, TATRG_EINVAL,
-              "gemm_tc: too many output tiles for the grid");
-  dim3 grid(unsigned(a.mtiles) * unsigned(a.ntiles), unsigned(split));
+  a.split = split;
+  const int64_t units = int64_t(a.mtiles) * a.ntiles * split;
+  TATRG_CHECK(units < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: too many work units");
+  // persistent: one CTA per SM (the shared-memory ring admits no second one)
+  static const int sms = []() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+      n = 1;
+    return n;
+  }();
+  dim3 grid(unsigned(std::min<int64_t>(units, sms)));
   const bool timed = st && st->timing;
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
   if (prec == 1) launch<1>(mahi, malo, mbhi, mblo, a, grid, s);
