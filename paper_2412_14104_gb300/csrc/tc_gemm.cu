@@ -6,12 +6,13 @@
 // ("3xTF32" / "BF16x3").  Flow per contraction:
 //   pack   : gather the multi-mode operand into a K-major, zero-padded [rows][K] panel of
 //            hi and lo values (one pass over HBM, coalesced writes);
-//   gemm   : 128 x BN output tile per CTA; warp 0 issues TMA loads of 64-byte K slices
-//            (SWIZZLE_64B) into a ring of shared-memory stages, one thread of warp 1
-//            issues tcgen05.mma (M = 128, N = BN) into a TMEM accumulator and frees a
-//            stage with tcgen05.commit, warps 2-5 read the accumulator with tcgen05.ld and
-//            write float64 results through the multi-mode C strides (atomic adds when K is
-//            split across CTAs);
+//   gemm   : persistent kernel, one CTA per SM walking 128 x 128 output tiles; warp 0
+//            issues TMA loads of 128-byte K slices (SWIZZLE_128B) into a ring of
+//            shared-memory stages, one thread of warp 1 issues tcgen05.mma (M = N = 128)
+//            into one of two TMEM chunk buffers and frees a stage with tcgen05.commit,
+//            sixteen epilogue warps fold every finished chunk (64 K elements) into
+//            double-float sums kept in TMEM and write float64 results through the
+//            multi-mode C strides (atomic adds when K is split across CTAs);
 //   every mbarrier wait is bounded in time; a wait that runs out raises an error flag,
 //   the CTA stops issuing work, frees its TMEM and returns.
 #include <cuda.h>
@@ -23,16 +24,19 @@ namespace tatrg {
 namespace {
 
 // stages (64-byte K slices) accumulated in one FP32 chain before a drain
-#ifndef TATRG_KC_TF32
-#define TATRG_KC_TF32 4
+// bytes of K per shared-memory stage row: one SWIZZLE_64B or SWIZZLE_128B atom row
+#ifndef TATRG_KSLICE
+#define TATRG_KSLICE 128
 #endif
-#ifndef TATRG_KC_BF16
-#define TATRG_KC_BF16 2
+// K elements accumulated in one FP32 chain before a drain
+#ifndef TATRG_CHAIN_K
+#define TATRG_CHAIN_K 64
 #endif
 
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 128;
-constexpr int KSLICE = 64;  // bytes of K per stage row (one SWIZZLE_64B atom)
+constexpr int KSLICE = TATRG_KSLICE;
+static_assert(KSLICE == 64 || KSLICE == 128, "stage rows are one 64- or 128-byte swizzle atom");
 constexpr int SMEM_BUDGET = 192 * 1024;
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s; a CTA gives up after 4 WAIT_NS
 
@@ -88,14 +92,15 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// K-major operand tile in shared memory, 64-byte rows, SWIZZLE_64B (8-row atoms of 512 B).
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+// K-major operand tile in shared memory, KSLICE-byte rows, swizzled in 8-row atoms of
+// 8 * KSLICE bytes (SWIZZLE_64B or SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
   uint64_t d = 0;
-  d |= uint64_t((saddr & 0x3FFFF) >> 4);  // start address, 16-byte units
-  d |= uint64_t(1) << 16;                 // leading byte offset (unused for this layout)
-  d |= uint64_t(512 >> 4) << 32;          // stride byte offset: next 8-row group
-  d |= uint64_t(1) << 46;                 // descriptor version
-  d |= uint64_t(4) << 61;                 // SWIZZLE_64B
+  d |= uint64_t((saddr & 0x3FFFF) >> 4);          // start address, 16-byte units
+  d |= uint64_t(1) << 16;                         // leading byte offset (unused for this layout)
+  d |= uint64_t((8 * KSLICE) >> 4) << 32;         // stride byte offset: next 8-row group
+  d |= uint64_t(1) << 46;                         // descriptor version
+  d |= uint64_t(KSLICE == 128 ? 2 : 4) << 61;     // SWIZZLE_128B : SWIZZLE_64B
   return d;
 }
 template <int PREC>
@@ -346,8 +351,8 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
             if (!mbar_wait(&full_bar[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
             tc_fence_after();
             const uint32_t base = smem_u32(smem + s * STAGE);
-            const uint64_t ahi = sdesc_sw64(base), alo = sdesc_sw64(base + A_TILE);
-            const uint64_t bhi = sdesc_sw64(base + 2 * A_TILE), blo = sdesc_sw64(base + 2 * A_TILE + B_TILE);
+            const uint64_t ahi = sdesc_sw(base), alo = sdesc_sw(base + A_TILE);
+            const uint64_t bhi = sdesc_sw(base + 2 * A_TILE), blo = sdesc_sw(base + 2 * A_TILE + B_TILE);
 #pragma unroll
             for (int kk = 0; kk < KSLICE / 32; ++kk) {  // 32 bytes of K per instruction
               const uint64_t off = uint64_t(kk * 2);
@@ -596,7 +601,8 @@ CUtensorMap make_map(void* base, int64_t rows, int64_t kp, int esize, int box_ro
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode_fn()(&m, prec == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                            2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           KSLICE == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   TATRG_CHECK(r == CUDA_SUCCESS, TATRG_ECUDA, "cuTensorMapEncodeTiled failed");
   return m;
@@ -607,7 +613,8 @@ void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& b
             const CUtensorMap& blo, const TcArgs& a, dim3 grid, cudaStream_t s) {
   constexpr int STAGE = 2 * TC_BM * KSLICE + 2 * TC_BN * KSLICE;
   constexpr int STAGES = SMEM_BUDGET / STAGE;
-  constexpr int KC = PREC == 1 ? TATRG_KC_TF32 : TATRG_KC_BF16;  // stages per FP32 chain
+  constexpr int KC = TATRG_CHAIN_K / (PREC == 1 ? KSLICE / 4 : KSLICE / 2);  // stages per FP32 chain
+  static_assert(KC >= 1, "an FP32 chain spans at least one stage");
   constexpr int SMEM = STAGES * STAGE + 1024;
   auto k = tc_gemm_kernel<PREC, KC, STAGES, 2>;
   static const cudaError_t attr =  // once per instantiation, thread-safe
