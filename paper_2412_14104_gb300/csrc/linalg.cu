@@ -10,17 +10,18 @@ namespace tatrg {
 namespace {
 
 // Right-looking Cholesky G + shift I = R^T R with the upper triangle of the working
-// matrix in shared memory (full n x n storage, n <= 160).  Step j: every thread takes
-// the pivot square root itself, row j is scaled into R's row j (and a shared copy), then
-// the trailing block subtracts the outer product of the scaled row: two block barriers per
-// step.  A pivot at or below 1e-14 of its original diagonal entry is a breakdown
-// (status 1).
+// matrix in shared memory (full n x n storage, n <= 160).  Step j: one thread takes the
+// pivot square root (FP64 square roots and divisions are scarce on this GPU, so they are
+// not repeated per thread), the threads scale row j, then the trailing block subtracts the
+// outer product of the scaled row.  A pivot at or below 1e-14 of its original diagonal
+// entry is a breakdown (status 1).
 __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, double* R,
                                                         int* status, double shift_rel) {
   extern __shared__ double W[];
-  __shared__ double shift;
+  __shared__ double shift, djj_s;
+  __shared__ int fail_s;
   __shared__ double red[32];
-  __shared__ double rowj[160];
+  __shared__ double ref[160];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int tx = tid & 31, ty = tid >> 5;  // 32 x 32 threads over (k, i)
   {
@@ -33,6 +34,7 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, 
       double t = 0.0;
       for (int w = 0; w < (nt >> 5); ++w) t += red[w];
       shift = shift_rel * t;
+      fail_s = 0;
     }
     __syncthreads();
   }
@@ -40,27 +42,28 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, 
   for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, k = e - (e / n) * n;
     W[e] = (k >= i) ? G[e] + (i == k ? sh : 0.0) : 0.0;
-  }
-  int fail = 0;
-  for (int j = 0; j < n; ++j) {
-    __syncthreads();
-    const double d = W[j * n + j];
-    const double ref = G[int64_t(j) * n + j] + sh;
-    if (!(d > 1e-14 * ref) || !(ref > 0.0)) { fail = 1; break; }  // uniform across the block
-    const double djj = sqrt(d);
-    for (int k = j + tid; k < n; k += nt) {
-      const double x = (k == j) ? djj : W[j * n + k] / djj;
-      rowj[k] = x;
-      W[j * n + k] = x;
-    }
-    __syncthreads();
-    for (int i = j + 1 + ty; i < n; i += 32) {
-      const double a = rowj[i];
-      for (int k = i + ((tx - (i - (j + 1))) & 31); k < n; k += 32)
-        W[i * n + k] = fma(-a, rowj[k], W[i * n + k]);
-    }
+    if (i == k) ref[i] = G[e] + sh;
   }
   __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const double d = W[j * n + j];
+      if (!(d > 1e-14 * ref[j]) || !(ref[j] > 0.0)) fail_s = 1;
+      else djj_s = sqrt(d);
+    }
+    __syncthreads();
+    if (fail_s) break;  // uniform across the block
+    const double djj = djj_s;
+    for (int k = j + tid; k < n; k += nt) W[j * n + k] = (k == j) ? djj : W[j * n + k] / djj;
+    __syncthreads();
+    for (int i = j + 1 + ty; i < n; i += 32) {
+      const double a = W[j * n + i];
+      for (int k = i + ((tx - (i - (j + 1))) & 31); k < n; k += 32)
+        W[i * n + k] = fma(-a, W[j * n + k], W[i * n + k]);
+    }
+    __syncthreads();
+  }
+  const int fail = fail_s;
   for (int e = tid; e < n * n; e += nt) R[e] = fail ? 0.0 : W[e];
   if (tid == 0) *status = fail;
 }

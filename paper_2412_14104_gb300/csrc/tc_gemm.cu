@@ -178,6 +178,33 @@ __device__ __forceinline__ constexpr uint32_t idesc() {
          (uint32_t(BN >> 3) << 17) | (uint32_t(TC_BM >> 4) << 24);
 }
 
+// float <-> double by IEEE-754 bit manipulation on the integer pipes: this GPU has few FP64
+// units, and a conversion on them costs as much as an FP64 add.  Values outside the
+// normal range of float (zero, subnormals, overflow, inf, nan) take the hardware
+// conversion.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 255u) {
+    if ((u << 1) == 0u) return __longlong_as_double(int64_t(uint64_t(u) << 32));  // signed zero
+    return double(f);
+  }
+  return __longlong_as_double(int64_t((uint64_t(u & 0x80000000u) << 32) | (uint64_t(e + 896u) << 52) |
+                                      (uint64_t(u & 0x7FFFFFu) << 29)));
+}
+// round to nearest, ties to even
+__device__ __forceinline__ float d2f_bits(double x) {
+  const uint64_t b = uint64_t(__double_as_longlong(x));
+  if ((b << 1) == 0u) return __uint_as_float(uint32_t(b >> 32));  // signed zero
+  const int e = int((b >> 52) & 0x7FFu) - 896;                     // biased float exponent
+  if (e <= 0 || e >= 255) return __double2float_rn(x);
+  const uint64_t m = b & 0xFFFFFFFFFFFFFull;
+  uint32_t f = (uint32_t(b >> 32) & 0x80000000u) | (uint32_t(e) << 23) | uint32_t(m >> 29);
+  const uint64_t rem = m & 0x1FFFFFFFull, half = 0x10000000ull;
+  if (rem > half || (rem == half && (f & 1u))) f += 1u;  // a carry into the exponent rounds correctly
+  return __uint_as_float(f);
+}
+
 struct TcArgs {
   DevModes mC;  // s1 = C stride of each M mode
   DevModes nC;  // s1 = C stride of each N mode
@@ -454,7 +481,8 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
           for (int j = 0; j < 16; ++j) {
             if (16 * part + j < ncols) {
               double* p = crow + co[j];
-              const double x = alpha * (double(__uint_as_float(vh[j])) + double(__uint_as_float(vl[j])));
+              double x = f2d_bits(__uint_as_float(vh[j])) + f2d_bits(__uint_as_float(vl[j]));
+              if (alpha != 1.0) x *= alpha;
               if (mode == 2) atomicAdd(p, x);
               else if (mode == 1) *p = fma(beta, *p, x);
               else *p = x;
@@ -490,13 +518,16 @@ constexpr int PK_R = 32, PK_K = 128;
 template <int PREC>
 __device__ __forceinline__ void pack_store(void* hi, void* lo, int64_t o, double x) {
   if (PREC == 1) {
-    const float h = tf32_rna(__double2float_rn(x));
-    const float l = tf32_rna(__double2float_rn(x - double(h)));
+    // split the float nearest to x (its 24 bits hold more than hi + lo keep)
+    const float f = d2f_bits(x);
+    const float h = tf32_rna(f);
+    const float l = tf32_rna(__fsub_rn(f, h));
     reinterpret_cast<float*>(hi)[o] = h;
     reinterpret_cast<float*>(lo)[o] = l;
   } else {
-    const __nv_bfloat16 h = __double2bfloat16(x);
-    const __nv_bfloat16 l = __double2bfloat16(x - double(__bfloat162float(h)));
+    const float f = d2f_bits(x);
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+    const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(f, __bfloat162float(h)));
     reinterpret_cast<__nv_bfloat16*>(hi)[o] = h;
     reinterpret_cast<__nv_bfloat16*>(lo)[o] = l;
   }
