@@ -182,6 +182,18 @@ typedef struct {
 tatrg_status tatrg_contract(const tatrg_contraction* c, int precision, const double* A,
                             const double* B, double* C, void* cuda_stream);
 
+/* tatrg_contract with B the Gaussian sketch of tatrg_gaussian (seed, stream_id, replica;
+ * element B[k, n] is sketch element number sum_i k_i k_sB[i] + sum_i n_i n_sB[i]), generated
+ * while the tensor-core operand is packed and never stored: the random test matrix of the
+ * randomized SVD (Halko et al. Alg. 4.4, used for the bond swap of Eq. 1, Table 1) drawn in
+ * the contraction's operand producer.  Only for the split precisions (precision 1 or 2,
+ * where Box-Muller runs in float arithmetic: the values equal tatrg_gaussian's rounded to
+ * float) and contractions large enough for the tensor cores (EINVAL otherwise).  The
+ * result equals tatrg_contract on that sketch rounded to float, stored.  Synchronises. */
+tatrg_status tatrg_contract_sketch(const tatrg_contraction* c, int precision, const double* A,
+                                   unsigned long long seed, uint32_t stream_id, uint32_t replica,
+                                   double* C, void* cuda_stream);
+
 /* Orthonormal basis of the columns of the row-major m x n matrix Y (m >= n): Y = Q R with
  * Q^T Q = 1 and R upper triangular with a non-negative diagonal when Y has full column
  * rank (CholeskyQR2 with shift); a rank-deficient Y returns k < n columns spanning its

@@ -72,6 +72,7 @@ def lib():
             "tatrg_last_step_info": [P, ctypes.POINTER(StepInfo)],
             "tatrg_gaussian": [U64, U32, U32, I64, I64, P, P],
             "tatrg_contract": [ctypes.POINTER(Contraction), I, P, P, P, P],
+            "tatrg_contract_sketch": [ctypes.POINTER(Contraction), I, P, U64, U32, U32, P, P],
             "tatrg_orth": [I, I64, I64, P, P, P, ctypes.POINTER(I), P],
             "tatrg_svd": [I64, I64, P, P, P, P, P],
             "tatrg_svd_noalloc": [I64, I64, P, P, P, P, P],
@@ -196,6 +197,31 @@ def gaussian(seed, stream_id, rows, cols, out, replica=0, stream=None):
     _check(lib().tatrg_gaussian(seed, stream_id, replica, rows, cols,
                                 ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def _contraction(m, n, k, alpha, beta):
+    c = Contraction()
+    for name, modes in (("m", m), ("n", n), ("k", k)):
+        assert len(modes) <= 4
+        full = list(modes) + [(1, 0, 0)] * (4 - len(modes))
+        s1, s2 = {"m": ("m_sA", "m_sC"), "n": ("n_sB", "n_sC"), "k": ("k_sA", "k_sB")}[name]
+        for i, (e, a, b) in enumerate(full):
+            getattr(c, name + "_ext")[i] = e
+            getattr(c, s1)[i] = a
+            getattr(c, s2)[i] = b
+    c.alpha, c.beta = alpha, beta
+    return c
+
+
+def contract_sketch(m, n, k, A, seed, stream_id, C, replica=0, alpha=1.0, beta=0.0,
+                    precision=TF32X3, stream=None):
+    """contract() with B the Gaussian sketch (seed, stream_id, replica) generated in the
+    tensor-core operand packer instead of read from memory (split precisions only)."""
+    c = _contraction(m, n, k, alpha, beta)
+    _check(lib().tatrg_contract_sketch(ctypes.byref(c), precision, ctypes.c_void_p(A.data_ptr()),
+                                       seed, stream_id, replica, ctypes.c_void_p(C.data_ptr()),
+                                       _stream_ptr(stream)))
+    return C
 
 
 def contract(m, n, k, A, B, C, alpha=1.0, beta=0.0, precision=FP64, stream=None):

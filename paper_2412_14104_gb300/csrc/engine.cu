@@ -12,16 +12,23 @@ int keep_count(const std::vector<double>& v, double rel, int64_t cap) {
   return int(n);
 }
 
-void Engine::gemm(const GemmDesc& d, const double* A, const double* B, double* C) {
+// Tensor cores for the large contractions of the split forms; the FP64 CUDA-core kernel
+// for everything small (where 128-row tiles would be mostly padding).
+static bool use_tc(const Engine& e, const GemmDesc& d) {
   const double M = double(d.m.total()), N = double(d.n.total()), K = double(d.k.total());
-  // Tensor cores for the large contractions of the split forms; the FP64 CUDA-core
-  // kernel for everything small (where 128-row tiles would be mostly padding).
-  if (prec != 0 && allow_tc && tc_available() && M * N * K >= 2.0e7 && M >= 32 && N >= 16 &&
-      K >= 16) {
-    gemm_tc(d, A, B, C, prec, s_, &st_);
-  } else {
-    gemm_f64(d, A, B, C, s_, &st_);
-  }
+  return e.prec != 0 && e.allow_tc && tc_available() && M * N * K >= 2.0e7 && M >= 32 &&
+         N >= 16 && K >= 16;
+}
+
+void Engine::gemm(const GemmDesc& d, const double* A, const double* B, double* C) {
+  if (use_tc(*this, d)) gemm_tc(d, A, B, C, prec, s_, &st_);
+  else gemm_f64(d, A, B, C, s_, &st_);
+}
+
+bool Engine::gemm_gauss_b(const GemmDesc& d, const double* A, const GaussSrc& g, double* C) {
+  if (!use_tc(*this, d)) return false;
+  gemm_tc(d, A, nullptr, C, prec, s_, &st_, &g);
+  return true;
 }
 
 void Engine::mm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta,

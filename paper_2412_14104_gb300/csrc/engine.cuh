@@ -40,6 +40,10 @@ class Engine {
   bool allow_tc = true;
 
   void gemm(const GemmDesc& d, const double* A, const double* B, double* C);
+  // C = A Omega with the Gaussian sketch Omega generated while the tensor-core operand is
+  // packed (never stored).  Only for contractions that take the split-precision path;
+  // returns false, having done nothing, otherwise.
+  bool gemm_gauss_b(const GemmDesc& d, const double* A, const GaussSrc& g, double* C);
   // row-major C (M x N) = alpha op(A) op(B) + beta C, op = transpose when flag set;
   // lda etc. are the row lengths of the stored matrices.
   void mm(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, bool ta,

@@ -87,7 +87,14 @@ void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S,
 bool tc_available();
 // reads (and optionally clears) the flag a timed-out tensor-core wait raises
 int tc_error_flag(bool reset);
+// A Gaussian sketch operand that is generated while packing instead of read from memory
+// (the element index is the operand offset the modes give).
+struct GaussSrc {
+  uint64_t seed = 0;
+  uint32_t sid = 0, replica = 0;
+};
+// gen_b: B is that sketch (B must be null)
 void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int prec,
-             cudaStream_t s, Stats* st);
+             cudaStream_t s, Stats* st, const GaussSrc* gen_b = nullptr);
 
 }  // namespace tatrg

@@ -2,6 +2,7 @@
 // for small contractions in every form, the Philox Gaussian sketch, and the elementwise
 // and reduction helpers of the RG step.
 #include "kernels.cuh"
+#include "philox.cuh"
 
 namespace tatrg {
 
@@ -263,38 +264,16 @@ void gemm_f64(const GemmDesc& d0, const double* A, const double* B, double* C, c
 }
 
 // ---------------------------------------------------------------------------------
-// Philox4x32-10 (Salmon et al., SC'11) + Box-Muller.  One thread per output pair.
+// Philox4x32-10 + Box-Muller (philox.cuh).  One thread per output pair.
 namespace {
-__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2,
-                                             uint32_t& c3, uint32_t k0, uint32_t k1) {
-  const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
-  uint32_t hi0 = __umulhi(m0, c0), lo0 = m0 * c0;
-  uint32_t hi1 = __umulhi(m1, c2), lo1 = m1 * c2;
-  uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
-  c0 = n0;
-  c1 = lo1;
-  c2 = n2;
-  c3 = lo0;
-}
-
-__device__ __forceinline__ double u53(uint32_t a, uint32_t b) {
-  return (double(a >> 5) * 67108864.0 + double(b >> 6) + 0.5) * (1.0 / 9007199254740992.0);
-}
-
 __global__ void gaussian_kernel(uint64_t seed, uint32_t sid, uint32_t replica, int64_t n,
                                 double* out) {
   const int64_t npairs = (n + 1) / 2;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npairs;
        p += int64_t(gridDim.x) * blockDim.x) {
-    uint32_t c0 = uint32_t(p), c1 = uint32_t(uint64_t(p) >> 32), c2 = replica,
-             c3 = uint32_t(seed >> 32);
-    uint32_t k0 = uint32_t(seed), k1 = sid;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-      if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-      philox_round(c0, c1, c2, c3, k0, k1);
-    }
-    double u1 = u53(c0, c1), u2 = u53(c2, c3);
+    uint32_t w[4];
+    philox4x32_10(seed, sid, replica, p, w);
+    double u1 = u53(w[0], w[1]), u2 = u53(w[2], w[3]);
     double rad = sqrt(-2.0 * log(u1));
     double ang = 2.0 * 3.141592653589793 * u2;
     out[2 * p] = rad * cos(ang);
@@ -302,31 +281,18 @@ __global__ void gaussian_kernel(uint64_t seed, uint32_t sid, uint32_t replica, i
   }
 }
 
-// The same stream with Box-Muller evaluated in float arithmetic (relative error ~1e-7),
-// for sketches that feed split-precision contractions, where the operand is rounded to
-// two tensor-core numbers (~2^-22 relative) anyway.  The uniforms are the same 53-bit
-// values, rounded to float (never to zero: the smallest is 2^-54).
+// The same stream with Box-Muller in float arithmetic (gauss_pair_f32).
 __global__ void gaussian_f32_kernel(uint64_t seed, uint32_t sid, uint32_t replica, int64_t n,
                                     double* out) {
   const int64_t npairs = (n + 1) / 2;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < npairs;
        p += int64_t(gridDim.x) * blockDim.x) {
-    uint32_t c0 = uint32_t(p), c1 = uint32_t(uint64_t(p) >> 32), c2 = replica,
-             c3 = uint32_t(seed >> 32);
-    uint32_t k0 = uint32_t(seed), k1 = sid;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-      if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-      philox_round(c0, c1, c2, c3, k0, k1);
-    }
-    const float u1 = float(u53(c0, c1)), u2 = float(u53(c2, c3));
-    const float rad = sqrtf(-2.0f * logf(u1));
-    float sn, cs;
-    sincospif(2.0f * u2, &sn, &cs);  // angle 2 pi u2, reduced exactly in units of pi
+    float z0, z1;
+    gauss_pair_f32(seed, sid, replica, p, z0, z1);
     if (2 * p + 1 < n) {
-      reinterpret_cast<double2*>(out)[p] = make_double2(double(rad * cs), double(rad * sn));
+      reinterpret_cast<double2*>(out)[p] = make_double2(double(z0), double(z1));
     } else {
-      out[2 * p] = double(rad * cs);
+      out[2 * p] = double(z0);
     }
   }
 }

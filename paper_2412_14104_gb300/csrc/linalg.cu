@@ -10,15 +10,16 @@ namespace tatrg {
 namespace {
 
 // Right-looking Cholesky G + shift I = R^T R with the upper triangle of the working
-// matrix in shared memory (full n x n storage, n <= 160).  Step j: one thread takes the
-// pivot square root (FP64 square roots and divisions are scarce on this GPU, so they are
-// not repeated per thread), the threads scale row j, then the trailing block subtracts the
-// outer product of the scaled row.  A pivot at or below 1e-14 of its original diagonal
-// entry is a breakdown (status 1).
+// matrix in shared memory (full n x n storage, n <= 160).  Step j scales row j by the
+// pivot square root, then subtracts the outer product of the scaled row from the trailing
+// block; the thread that updates the next diagonal entry takes its square root at once
+// (FP64 square roots and divisions are scarce on this GPU, so they are not repeated per
+// thread), which leaves two block barriers per step.  A pivot at or below 1e-14 of its
+// original diagonal entry is a breakdown (status 1).
 __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, double* R,
                                                         int* status, double shift_rel) {
   extern __shared__ double W[];
-  __shared__ double shift, djj_s;
+  __shared__ double shift, djj_s[2];
   __shared__ int fail_s;
   __shared__ double red[32];
   __shared__ double ref[160];
@@ -45,15 +46,17 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, 
     if (i == k) ref[i] = G[e] + sh;
   }
   __syncthreads();
+  // pivot j is checked and rooted by thread 0, which also updates entry (j, j) in step j - 1
+  auto pivot = [&](int j) {
+    const double d = W[j * n + j];
+    if (!(d > 1e-14 * ref[j]) || !(ref[j] > 0.0)) fail_s = 1;
+    else djj_s[j & 1] = sqrt(d);
+  };
+  if (tid == 0) pivot(0);
   for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const double d = W[j * n + j];
-      if (!(d > 1e-14 * ref[j]) || !(ref[j] > 0.0)) fail_s = 1;
-      else djj_s = sqrt(d);
-    }
     __syncthreads();
     if (fail_s) break;  // uniform across the block
-    const double djj = djj_s;
+    const double djj = djj_s[j & 1];
     for (int k = j + tid; k < n; k += nt) W[j * n + k] = (k == j) ? djj : W[j * n + k] / djj;
     __syncthreads();
     for (int i = j + 1 + ty; i < n; i += 32) {
@@ -61,8 +64,9 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, 
       for (int k = i + ((tx - (i - (j + 1))) & 31); k < n; k += 32)
         W[i * n + k] = fma(-a, W[j * n + k], W[i * n + k]);
     }
-    __syncthreads();
+    if (tid == 0 && j + 1 < n) pivot(j + 1);  // thread 0 updated entry (j + 1, j + 1) above
   }
+  __syncthreads();
   const int fail = fail_s;
   for (int e = tid; e < n * n; e += nt) R[e] = fail ? 0.0 : W[e];
   if (tid == 0) *status = fail;
@@ -71,20 +75,35 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, 
 // Inverse of an upper-triangular matrix: column c of X = R^-1 is the back substitution
 // R x = e_c, independent of the other columns, so one warp solves one column (x in the
 // warp's slice of shared memory, the inner products split across lanes); no block-wide
-// barrier is needed.
+// barrier is needed.  RS: the leading (cmax + 1) x (cmax + 1) block of R that the block's
+// columns need is first copied to shared memory, so each back-substitution step reads
+// shared memory instead of L2 (the same arithmetic in the same order).
+template <bool RS>
 __global__ void __launch_bounds__(128) tri_inverse_kernel(const double* R, int n, double* X) {
   extern __shared__ double xs[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = blockIdx.x * 4 + w;
+  const int cmax = min(n - 1, blockIdx.x * 4 + 3);
+  const int ld = RS ? cmax + 1 : n;
+  const double* Rm = R;
+  if (RS) {
+    double* Rs = xs + 4 * n;
+    for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+      const int i = e / ld, k = e - (e / ld) * ld;
+      Rs[e] = (k >= i) ? R[int64_t(i) * n + k] : 0.0;
+    }
+    __syncthreads();
+    Rm = Rs;
+  }
   if (c >= n) return;
   double* x = xs + w * n;
   for (int i = lane; i < n; i += 32) x[i] = 0.0;
   __syncwarp();
   for (int i = c; i >= 0; --i) {
     double acc = 0.0;
-    for (int k = i + 1 + lane; k <= c; k += 32) acc += R[int64_t(i) * n + k] * x[k];
+    for (int k = i + 1 + lane; k <= c; k += 32) acc += Rm[int64_t(i) * ld + k] * x[k];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[i] = ((i == c ? 1.0 : 0.0) - acc) / R[int64_t(i) * n + i];
+    if (lane == 0) x[i] = ((i == c ? 1.0 : 0.0) - acc) / Rm[int64_t(i) * ld + i];
     __syncwarp();
   }
   for (int i = lane; i < n; i += 32) X[int64_t(i) * n + c] = x[i];
@@ -341,6 +360,8 @@ __device__ bool grid_barrier(unsigned* bar) {
   return ok != 0;
 }
 
+constexpr int kCache = 4;  // column elements per thread kept in registers
+
 // The same rotations as tall_jacobi_round_kernel, all sweeps in one cooperative launch:
 // block b handles pairs b, b + gridDim.x, ... of each round and a grid-wide barrier
 // separates rounds.  All blocks decide convergence from the same flag after a barrier.
@@ -363,12 +384,41 @@ __global__ void __launch_bounds__(256) coop_jacobi_kernel(double* Ac, int64_t m,
         else { p = (r + k) % (N - 1); q = (r + N - 1 - k) % (N - 1); }
         double* ap = Ac + int64_t(p) * m;
         double* aq = Ac + int64_t(q) * m;
+        double* vp = Vc + int64_t(p) * N;
+        double* vq = Vc + int64_t(q) * N;
+        // short columns stay in registers from the inner products to the rotation, and the
+        // V columns are fetched before the inner products so their latency overlaps them
+        const bool cached = m <= kCache * int64_t(blockDim.x) && N <= kCache * int(blockDim.x);
+        double xs[kCache], ys[kCache], vxs[kCache], vys[kCache];
         double al = 0.0, be = 0.0, ga = 0.0;
-        for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-          double x = ap[i], y = aq[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga = fma(x, y, ga);
+        if (cached) {
+#pragma unroll
+          for (int c = 0; c < kCache; ++c) {
+            const int i = threadIdx.x + c * blockDim.x;
+            vxs[c] = i < N ? vp[i] : 0.0;
+            vys[c] = i < N ? vq[i] : 0.0;
+          }
+#pragma unroll
+          for (int c = 0; c < kCache; ++c) {
+            const int64_t i = threadIdx.x + int64_t(c) * blockDim.x;
+            xs[c] = i < m ? ap[i] : 0.0;
+            ys[c] = i < m ? aq[i] : 0.0;
+          }
+#pragma unroll
+          for (int c = 0; c < kCache; ++c) {
+            if (threadIdx.x + int64_t(c) * blockDim.x < m) {
+              al = fma(xs[c], xs[c], al);
+              be = fma(ys[c], ys[c], be);
+              ga = fma(xs[c], ys[c], ga);
+            }
+          }
+        } else {
+          for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+            double x = ap[i], y = aq[i];
+            al = fma(x, x, al);
+            be = fma(y, y, be);
+            ga = fma(x, y, ga);
+          }
         }
         for (int o = 16; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
@@ -393,17 +443,36 @@ __global__ void __launch_bounds__(256) coop_jacobi_kernel(double* Ac, int64_t m,
         __syncthreads();
         if (doit) {
           const double c = cs[0], sn = cs[1];
-          for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
-            double x = ap[i], y = aq[i];
-            ap[i] = c * x - sn * y;
-            aq[i] = sn * x + c * y;
-          }
-          double* vp = Vc + int64_t(p) * N;
-          double* vq = Vc + int64_t(q) * N;
-          for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            double x = vp[i], y = vq[i];
-            vp[i] = c * x - sn * y;
-            vq[i] = sn * x + c * y;
+          if (cached) {
+#pragma unroll
+            for (int cc = 0; cc < kCache; ++cc) {
+              const int64_t i = threadIdx.x + int64_t(cc) * blockDim.x;
+              if (i < m) {
+                const double x = xs[cc], y = ys[cc];
+                ap[i] = c * x - sn * y;
+                aq[i] = sn * x + c * y;
+              }
+            }
+#pragma unroll
+            for (int cc = 0; cc < kCache; ++cc) {
+              const int i = threadIdx.x + cc * blockDim.x;
+              if (i < N) {
+                const double x = vxs[cc], y = vys[cc];
+                vp[i] = c * x - sn * y;
+                vq[i] = sn * x + c * y;
+              }
+            }
+          } else {
+            for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+              double x = ap[i], y = aq[i];
+              ap[i] = c * x - sn * y;
+              aq[i] = sn * x + c * y;
+            }
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+              double x = vp[i], y = vq[i];
+              vp[i] = c * x - sn * y;
+              vq[i] = sn * x + c * y;
+            }
           }
         }
         __syncthreads();
@@ -451,7 +520,14 @@ void tri_inverse(const double* R, int n, double* Rinv, cudaStream_t s) {
   check_extent(R, int64_t(n) * n - 1, sizeof(double), "tri_inverse input");
   check_extent(Rinv, int64_t(n) * n - 1, sizeof(double), "tri_inverse output");
   TATRG_CHECK(n >= 1 && n <= 1024, TATRG_EINVAL, "tri_inverse: n must be <= 1024");
-  tri_inverse_kernel<<<(n + 3) / 4, 128, 4 * n * sizeof(double), s>>>(R, n, Rinv);
+  if (n <= 160) {
+    static const cudaError_t attr = cudaFuncSetAttribute(  // once, thread-safe
+        tri_inverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (160 * 160 + 4 * 160) * 8);
+    TATRG_CUDA(attr);
+    tri_inverse_kernel<true><<<(n + 3) / 4, 128, size_t(n * n + 4 * n) * sizeof(double), s>>>(R, n, Rinv);
+  } else {
+    tri_inverse_kernel<false><<<(n + 3) / 4, 128, 4 * n * sizeof(double), s>>>(R, n, Rinv);
+  }
   TATRG_CUDA(cudaGetLastError());
 }
 

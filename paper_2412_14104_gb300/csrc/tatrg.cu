@@ -498,8 +498,14 @@ void tatrg_ctx::rg_step() {
     sw = eng.svd(mid.d(), rows, rows);
     if (T) swt = eng.svd_tan(midd.d(), rows, rows, sw, keep_count(sw.s, 1e-14, sw.r), multiplet_groups(sw.s, tau));
   } else {
-    DevBuf om(rows * ell * sizeof(double), st);
-    gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st, eng.prec != 0);
+    // the swap sketch Omega (rows x ell), stored only when a product needs it from memory
+    DevBuf om;
+    const GaussSrc swap_sketch{p.seed, stream_id(step, KIND_SWAP), replica};
+    auto materialise = [&]() {
+      if (!om.empty()) return;
+      om = DevBuf(rows * ell * sizeof(double), st);
+      gaussian(swap_sketch.seed, swap_sketch.sid, swap_sketch.replica, rows * ell, om.d(), st, eng.prec != 0);
+    };
     // M X: W[a,k,b,p] = sum_j Bs[a,k,j] X[(b,j),p];  Y[(a,i),p] = sum_{k,b} As[k,i,b] W[a,k,b,p]
     // (with any pair of factors Ap, Bp in place of As, Bs; beta = 1 accumulates into Y)
     auto apply_g = [&](const double* Ap, const double* Bp, const double* X, int64_t w, double* Y,
@@ -581,7 +587,17 @@ void tatrg_ctx::rg_step() {
       };
       DMat W0;
       W0.buf = dalloc(nL * ell, st);
-      apply_R(om.d(), ell, W0.p());
+      {
+        // W0 = R Omega; in split precision the sketch is generated in the operand packer
+        const GemmDesc gr = G(modes({{Da_ * D0, I, Da_ * ell}}), modes({{Da_, I * ell, ell}, {ell, 1, 1}}),
+                              modes({{I, 1, ell}}));
+        if (eng.gemm_gauss_b(gr, Bs.d(), swap_sketch, W0.p())) {
+          count(ST_SWAP, gr);
+        } else {
+          materialise();
+          apply_R(om.d(), ell, W0.p());
+        }
+      }
       om.release();
       Engine::MetricOrth Qm = eng.orth_metric(W0.p(), nL, ell, metric_L);
       bool ok = Qm.ok;
@@ -624,10 +640,7 @@ void tatrg_ctx::rg_step() {
       }
     }
     if (!done) {
-      if (om.empty()) {
-        om = DevBuf(rows * ell * sizeof(double), st);
-        gaussian(p.seed, stream_id(step, KIND_SWAP), replica, rows * ell, om.d(), st, eng.prec != 0);
-      }
+      materialise();
       if (T) {
         Engine::RsvdT r = eng.rsvd_t(apply, rapply, apply_d, rapply_d, rows, rows, ell, p.q, om.d(), tau);
         sw = std::move(r.e);
@@ -1467,6 +1480,42 @@ tatrg_status tatrg_gaussian(unsigned long long seed, uint32_t sid, uint32_t repl
   return guard(nullptr, [&] {
     TATRG_CHECK(out && rows >= 0 && cols >= 0, TATRG_EINVAL, "tatrg_gaussian: bad argument");
     gaussian(seed, sid, replica, rows * cols, out, static_cast<cudaStream_t>(stream));
+  });
+}
+
+namespace {
+GemmDesc desc_of(const tatrg_contraction* c) {
+  GemmDesc g;
+  g.m = modes({{c->m_ext[0], c->m_sA[0], c->m_sC[0]}, {c->m_ext[1], c->m_sA[1], c->m_sC[1]},
+               {c->m_ext[2], c->m_sA[2], c->m_sC[2]}, {c->m_ext[3], c->m_sA[3], c->m_sC[3]}});
+  g.n = modes({{c->n_ext[0], c->n_sB[0], c->n_sC[0]}, {c->n_ext[1], c->n_sB[1], c->n_sC[1]},
+               {c->n_ext[2], c->n_sB[2], c->n_sC[2]}, {c->n_ext[3], c->n_sB[3], c->n_sC[3]}});
+  g.k = modes({{c->k_ext[0], c->k_sA[0], c->k_sB[0]}, {c->k_ext[1], c->k_sA[1], c->k_sB[1]},
+               {c->k_ext[2], c->k_sA[2], c->k_sB[2]}, {c->k_ext[3], c->k_sA[3], c->k_sB[3]}});
+  for (int i = 0; i < 4; ++i)
+    TATRG_CHECK(c->m_ext[i] >= 1 && c->n_ext[i] >= 1 && c->k_ext[i] >= 1, TATRG_EINVAL,
+                "tatrg_contract: extents must be >= 1");
+  g.alpha = c->alpha;
+  g.beta = c->beta;
+  return g;
+}
+}  // namespace
+
+tatrg_status tatrg_contract_sketch(const tatrg_contraction* c, int precision, const double* A,
+                                   unsigned long long seed, uint32_t sid, uint32_t replica, double* C,
+                                   void* stream) {
+  return guard(nullptr, [&] {
+    TATRG_CHECK(c && A && C, TATRG_EINVAL, "tatrg_contract_sketch: null argument");
+    TATRG_CHECK(precision == 1 || precision == 2, TATRG_EINVAL,
+                "tatrg_contract_sketch: needs a split precision (1 or 2)");
+    const GemmDesc g = desc_of(c);
+    Engine e(static_cast<cudaStream_t>(stream));
+    e.prec = precision;
+    const GaussSrc gs{seed, sid, replica};
+    TATRG_CHECK(e.gemm_gauss_b(g, A, gs, C), TATRG_EINVAL,
+                "tatrg_contract_sketch: contraction too small for the tensor-core path");
+    TATRG_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    TATRG_CHECK(tc_error_flag(true) == 0, TATRG_ETIMEOUT, "a tensor-core pipeline wait timed out");
   });
 }
 

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
+#include "philox.cuh"
 
 namespace tatrg {
 namespace {
@@ -533,11 +534,24 @@ __device__ __forceinline__ void pack_store(void* hi, void* lo, int64_t o, double
   }
 }
 
-template <int PREC>
+// GEN: the operand is the Gaussian sketch whose element index is the offset the modes
+// give (philox.cuh, float Box-Muller); src is not read.
+template <int PREC, bool GEN>
+__device__ __forceinline__ double operand_at(const double* __restrict__ src, const GaussSrc& gs,
+                                             int64_t off) {
+  if (GEN) {
+    float z0, z1;
+    gauss_pair_f32(gs.seed, gs.sid, gs.replica, off >> 1, z0, z1);
+    return double((off & 1) ? z1 : z0);
+  }
+  return __ldg(src + off);
+}
+
+template <int PREC, bool GEN>
 __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ src, DevModes rm,
                                                    DevModes km, int64_t R, int64_t K, int64_t Kp,
                                                    int64_t ktiles, int64_t ntiles, void* hi,
-                                                   void* lo, int r_contig) {
+                                                   void* lo, int r_contig, GaussSrc gs) {
   __shared__ int64_t roff[PK_R], koff[PK_K];
   __shared__ double tile[PK_R][PK_K + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;  // 8 warps
@@ -555,7 +569,37 @@ __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ sr
       koff[j] = a;
     }
     __syncthreads();
-    if (!r_contig) {
+    if (GEN) {
+      // generated sketch: warp w takes the row pairs (2w, 2w + 1), (2w + 16, 2w + 17); when
+      // the two rows hold consecutive sketch elements 2c, 2c + 1 (the row mode is the
+      // innermost one), one Philox call gives both
+#pragma unroll
+      for (int i = 0; i < PK_R / 16; ++i) {
+        const int rr = 2 * (warp + 8 * i);
+        const int64_t r = r0 + rr;
+#pragma unroll
+        for (int j = 0; j < PK_K / 32; ++j) {
+          const int kk = lane + 32 * j;
+          const int64_t k = k0 + kk;
+          if (k >= Kp) continue;
+          double v0 = 0.0, v1 = 0.0;
+          if (k < K) {
+            const int64_t o0 = roff[rr] + koff[kk], o1 = roff[rr + 1] + koff[kk];
+            if (r < R && r + 1 < R && o1 == o0 + 1 && (o0 & 1) == 0) {
+              float z0, z1;
+              gauss_pair_f32(gs.seed, gs.sid, gs.replica, o0 >> 1, z0, z1);
+              v0 = double(z0);
+              v1 = double(z1);
+            } else {
+              if (r < R) v0 = operand_at<PREC, true>(src, gs, o0);
+              if (r + 1 < R) v1 = operand_at<PREC, true>(src, gs, o1);
+            }
+          }
+          pack_store<PREC>(hi, lo, r * Kp + k, v0);
+          pack_store<PREC>(hi, lo, (r + 1) * Kp + k, v1);
+        }
+      }
+    } else if (!r_contig) {
       // warp w: rows w, w + 8, ...; lanes along K (coalesced reads and writes)
 #pragma unroll
       for (int i = 0; i < PK_R / 8; ++i) {
@@ -565,7 +609,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ sr
 #pragma unroll
         for (int j = 0; j < PK_K / 32; ++j) {
           const int kk = lane + 32 * j;
-          v[j] = (r < R && k0 + kk < K) ? __ldg(src + roff[rr] + koff[kk]) : 0.0;
+          v[j] = (r < R && k0 + kk < K) ? operand_at<PREC, GEN>(src, gs, roff[rr] + koff[kk]) : 0.0;
         }
 #pragma unroll
         for (int j = 0; j < PK_K / 32; ++j) {
@@ -579,7 +623,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ sr
       for (int i = 0; i < PK_K / 8; ++i) {
         const int kk = warp + 8 * i;
         const bool ok = (r0 + lane < R) && (k0 + kk < K);
-        tile[lane][kk] = ok ? __ldg(src + roff[lane] + koff[kk]) : 0.0;
+        tile[lane][kk] = ok ? operand_at<PREC, GEN>(src, gs, roff[lane] + koff[kk]) : 0.0;
       }
       __syncthreads();
 #pragma unroll
@@ -685,12 +729,19 @@ int tc_error_flag(bool reset) {
 }
 
 void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int prec,
-             cudaStream_t s, Stats* st) {
+             cudaStream_t s, Stats* st, const GaussSrc* gen_b) {
   TATRG_CHECK(prec == 1 || prec == 2, TATRG_EINVAL, "gemm_tc: precision must be TF32X3 or BF16X3");
   TATRG_CHECK(tc_available(), TATRG_ENOTIMPL, "gemm_tc: tcgen05 path needs an sm_103 GPU");
   const int64_t M = d.m.total(), N = d.n.total(), K = d.k.total();
   if (M == 0 || N == 0) return;
-  check_gemm(d, A, B, C);
+  if (gen_b) {
+    TATRG_CHECK(B == nullptr, TATRG_EINVAL, "gemm_tc: a generated B operand takes no pointer");
+    check_extent(A, max_off0(d.m) + max_off0(d.k), sizeof(double), "operand A");
+    check_extent(C, max_off1(d.m) + max_off1(d.n), sizeof(double), "result C");
+  } else {
+    check_gemm(d, A, B, C);
+  }
+  const GaussSrc no_gen{};
   const int esize = prec == 1 ? 4 : 2;
   const int kelem = KSLICE / esize;
   const int BN = TC_BN;
@@ -708,11 +759,11 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     const int rc = (d.m.n > 0 && d.m.s0[d.m.n - 1] == 1 && !(d.k.n > 0 && d.k.s0[d.k.n - 1] == 1)) ? 1 : 0;
     const int64_t kt = cdiv(Kp, PK_K), ta = (Mp / PK_R) * kt;
     const int ga = int(std::min<int64_t>(ta, 152 * 6));
-    if (prec == 1) pack_kernel<1><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
-    else pack_kernel<2><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc);
+    if (prec == 1) pack_kernel<1, false><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc, no_gen);
+    else pack_kernel<2, false><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc, no_gen);
     TATRG_CUDA(cudaGetLastError());
     // a Gram (B is A read the same way) reuses A's panels
-    bool same = (A == B) && Np == Mp && d.m.n == d.n.n && d.k.n > 0;
+    bool same = !gen_b && (A == B) && Np == Mp && d.m.n == d.n.n && d.k.n > 0;
     for (int i = 0; same && i < d.m.n; ++i) same = d.m.ext[i] == d.n.ext[i] && d.m.s0[i] == d.n.s0[i];
     for (int i = 0; same && i < d.k.n; ++i) same = d.k.s0[i] == d.k.s1[i];
     if (same) {
@@ -725,8 +776,13 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     const int64_t tb = (Np / PK_R) * kt;
     const int gb = int(std::min<int64_t>(tb, 152 * 6));
     if (!same) {
-      if (prec == 1) pack_kernel<1><<<gb, 256, 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
-      else pack_kernel<2><<<gb, 256, 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb);
+      if (gen_b) {
+        if (prec == 1) pack_kernel<1, true><<<gb, 256, 0, s>>>(nullptr, rn, kn, N, K, Kp, kt, tb, bhi, blo, 0, *gen_b);
+        else pack_kernel<2, true><<<gb, 256, 0, s>>>(nullptr, rn, kn, N, K, Kp, kt, tb, bhi, blo, 0, *gen_b);
+      } else {
+        if (prec == 1) pack_kernel<1, false><<<gb, 256, 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb, no_gen);
+        else pack_kernel<2, false><<<gb, 256, 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb, no_gen);
+      }
       TATRG_CUDA(cudaGetLastError());
     }
   }

@@ -183,3 +183,36 @@ def test_contract_tensor_core_split_k_gram(torch, prec):
     err = _tc_case(torch, prec, n, n, m, [(n, 1, n)], [(n, 1, 1)], [(m, n, n)], Y, Y, want)
     # each CTA sums ~1e3 positive products in the FP32 accumulator before the FP64 reduction
     assert err < 10 * TC_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+def test_sketch_generated_in_the_operand_packer(torch, prec):
+    """W = R Omega with the Gaussian sketch drawn while the tensor-core operand is packed
+    (float Box-Muller, never stored) against the oracle's product with its float64 sketch,
+    and against the same contraction on the stored float64 sketch of tatrg_gaussian.
+    Shapes as in the bond swap: R[(a,k), j], Omega[(b,j), p], W[(a,k), (b,p)], ragged tiles."""
+    rng = np.random.default_rng(21)
+    Dak, J, Db, ell = 150, 1500, 3, 36  # M N K = 2.4e7: the tensor-core path
+    R = rng.standard_normal((Dak, J))
+    seed, sid, rep = 7, 0x305, 2
+    m = [(Dak, J, Db * ell)]
+    n = [(Db, J * ell, ell), (ell, 1, 1)]
+    k = [(J, 1, ell)]
+    Om = torch.empty(Db * J * ell, dtype=torch.float64, device="cuda")
+    tg.gaussian(seed, sid, Db * J, ell, Om, replica=rep)
+    W1 = torch.zeros((Dak, Db * ell), dtype=torch.float64, device="cuda")
+    W2 = torch.zeros_like(W1)
+    dR = _dev(torch, R)
+    tg.contract(m, n, k, dR, Om, W1, precision=prec)
+    tg.contract_sketch(m, n, k, dR, seed, sid, W2, replica=rep, precision=prec)
+    torch.cuda.synchronize()
+    om = philox.gaussian(seed, sid, Db * J, ell, replica=rep).reshape(Db, J, ell)
+    want = np.einsum("aj,bjp->abp", R, om).reshape(Dak, Db * ell)
+    got1, got2 = W1.cpu().numpy(), W2.cpu().numpy()
+    scale = np.max(np.abs(want))
+    assert np.max(np.abs(got2 - want)) / scale < TC_TOL[prec]
+    assert np.max(np.abs(got1 - want)) / scale < TC_TOL[prec]
+    # float and float64 Box-Muller differ by ~1e-7 relative, below the operand split
+    assert np.max(np.abs(got2 - got1)) / scale < TC_TOL[prec]
+    with pytest.raises(tg.TatrgError):
+        tg.contract_sketch(m, n, k, dR, seed, sid, W2, precision=tg.FP64)
