@@ -280,9 +280,9 @@ def run_ours(args, world, rank, local):
     else:
         peak, note = bf16, "%s bf16 sustained" % src
     achieved = 3.0 * tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
-    traffic = None
+    traffic = None  # DRAM bytes per launch from the committed ncu capture of this workload
     prof = os.path.join(ROOT, "profiles", "tc_gemm_chi48_traffic.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and (chi, r) == (CHI, R) and prec == tg.TF32X3:
         with open(prof) as f:
             traffic = json.load(f).get("dram_bytes_per_launch")
 

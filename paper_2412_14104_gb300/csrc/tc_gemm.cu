@@ -253,8 +253,11 @@ struct Unit {
   int64_t m0, n0;
   int kb0, nk;
 };
+#ifndef TATRG_GROUP_M
+#define TATRG_GROUP_M 8
+#endif
 __device__ __forceinline__ Unit unit_of(const TcArgs& g, int u) {
-  constexpr int GROUP_M = 8;
+  constexpr int GROUP_M = TATRG_GROUP_M;
   const int tiles = g.mtiles * g.ntiles;
   const int sidx = u / tiles, b = u - sidx * tiles;
   const int per_group = GROUP_M * g.ntiles;
