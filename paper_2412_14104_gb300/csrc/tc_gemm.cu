@@ -215,6 +215,7 @@ struct TcArgs {
   int split;           // K ranges per tile; work unit u = split index * tiles + tile
   double alpha, beta;
   int atomic;
+  int n_contig;  // the C offset of output column n is n (the N modes run contiguously in C)
   double* C;
 };
 
@@ -312,6 +313,9 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[NBUF], acc_empty[NBUF], fin_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int64_t col_off[BN];
+  // per epilogue warp: a 32-row x 8-column slice of doubles (XOR-swizzled by row), through
+  // which the warp turns its row-per-lane values into row-contiguous stores
+  __shared__ __align__(16) double epi_stage[EPI_WARPS * 32 * 8];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int units = g.mtiles * g.ntiles * g.split;
@@ -469,27 +473,67 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
         const bool in_rows = (w.m0 + row) < g.M;
         int64_t roff = 0, dummy = 0;
         if (in_rows) mode_offsets(g.mC, w.m0 + row, dummy, roff);
-        double* const crow = g.C + roff;
-        const int64_t rem_ = g.N - (w.n0 + h * 32);
-        const int ncols = !in_rows ? 0 : (rem_ < 32 ? int(rem_) : 32);
         const double alpha = g.alpha, beta = g.beta;
         const int mode = g.atomic ? 2 : (beta != 0.0 ? 1 : 0);
+        if (g.n_contig && mode != 2) {
+          // coalesced: each slice of 8 columns goes through shared memory so that eight
+          // lanes write 64 contiguous bytes of one row (four rows per store instruction)
+          double* const stg = epi_stage + (warp - 2) * 256;
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
-          uint32_t vh[16], vl[16];
-          tmem_ld16_nowait(t_hi + uint32_t(16 * part), vh);
-          tmem_ld16_nowait(t_lo + uint32_t(16 * part), vl);
-          tmem_wait_ld();
-          const int64_t* const co = col_off + h * 32 + 16 * part;
+          for (int part = 0; part < 2; ++part) {
+            if (w.n0 + h * 32 + 16 * part >= g.N) break;  // the rest of this warp's columns are padding
+            uint32_t vh[16], vl[16];
+            tmem_ld16_nowait(t_hi + uint32_t(16 * part), vh);
+            tmem_ld16_nowait(t_lo + uint32_t(16 * part), vl);
+            tmem_wait_ld();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (16 * part + j < ncols) {
-              double* p = crow + co[j];
-              double x = f2d_bits(__uint_as_float(vh[j])) + f2d_bits(__uint_as_float(vl[j]));
-              if (alpha != 1.0) x *= alpha;
-              if (mode == 2) atomicAdd(p, x);
-              else if (mode == 1) *p = fma(beta, *p, x);
-              else *p = x;
+            for (int half = 0; half < 2; ++half) {
+              if (w.n0 + h * 32 + 16 * part + 8 * half >= g.N) break;
+              __syncwarp();
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                const int j = 8 * half + c;
+                double x = f2d_bits(__uint_as_float(vh[j])) + f2d_bits(__uint_as_float(vl[j]));
+                if (alpha != 1.0) x *= alpha;
+                stg[lane * 8 + (c ^ (lane & 7))] = x;
+              }
+              __syncwarp();
+              const int cb = h * 32 + 16 * part + 8 * half;  // tile column of the slice
+              const int c = lane & 7;
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const int r = (lane >> 3) + 4 * i;  // row of the warp's 32
+                const int64_t rb = __shfl_sync(0xffffffffu, roff, r);
+                const int rin = __shfl_sync(0xffffffffu, in_rows ? 1 : 0, r);
+                const double v = stg[r * 8 + (c ^ (r & 7))];
+                if (rin && w.n0 + cb + c < g.N) {
+                  double* p = g.C + rb + col_off[cb + c];
+                  *p = (mode == 1) ? fma(beta, *p, v) : v;
+                }
+              }
+            }
+          }
+        } else {
+          double* const crow = g.C + roff;
+          const int64_t rem_ = g.N - (w.n0 + h * 32);
+          const int ncols = !in_rows ? 0 : (rem_ < 32 ? int(rem_) : 32);
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            uint32_t vh[16], vl[16];
+            tmem_ld16_nowait(t_hi + uint32_t(16 * part), vh);
+            tmem_ld16_nowait(t_lo + uint32_t(16 * part), vl);
+            tmem_wait_ld();
+            const int64_t* const co = col_off + h * 32 + 16 * part;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              if (16 * part + j < ncols) {
+                double* p = crow + co[j];
+                double x = f2d_bits(__uint_as_float(vh[j])) + f2d_bits(__uint_as_float(vl[j]));
+                if (alpha != 1.0) x *= alpha;
+                if (mode == 2) atomicAdd(p, x);
+                else if (mode == 1) *p = fma(beta, *p, x);
+                else *p = x;
+              }
             }
           }
         }
@@ -810,6 +854,12 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   a.alpha = d.alpha;
   a.beta = d.beta;
   a.atomic = split > 1 ? 1 : 0;
+  {
+    // C offset of column n equals n when the N modes chain contiguously in C
+    bool contig = d.n.n >= 1 && d.n.s1[d.n.n - 1] == 1;
+    for (int i = 0; contig && i + 1 < d.n.n; ++i) contig = d.n.s1[i] == d.n.s1[i + 1] * d.n.ext[i + 1];
+    a.n_contig = contig ? 1 : 0;
+  }
   a.C = C;
   if (split > 1) {
     scale_c_kernel<<<int(std::min<int64_t>(cdiv(M * N, 256), 4096)), 256, 0, s>>>(C, dev(d.m), dev(d.n), M, N, d.beta);
