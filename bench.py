@@ -129,27 +129,36 @@ def barrier(world):
 
 
 # --------------------------------------------------------------------------------------
+_ORACLE = {}  # the chi = 48 swap operator and sketch width, built once per process
+
+
 def oracle_sample(min_seconds=10.0):
     """Time the FP64 oracle's bond-swap operator (one product Mid @ Omega of the chi = 48
-    step) on a growing number of sketch columns until it takes ~min_seconds; return
-    (seconds per RG step extrapolated by flops, description, threads)."""
+    step) on a number of sketch columns that takes ~min_seconds; return (seconds per RG
+    step extrapolated by flops, description, threads).  Building the state and drawing the
+    sketch are not timed."""
     import numpy as np
     from oracle import trg
     from paper_2412_14104_gb300 import synth
-    A, s, B = synth.split_state(7, (CHI,) * 4, CHI)
-    Dk, I, Da = CHI, CHI ** 3, CHI
-    As = A.reshape(Dk, I, Da) * s[None, None, :]
-    Bs = B.reshape(Da, Dk, I) * s[:, None, None]
-    op = trg.SwapOp(As, Bs, None)
-    cols = 1
+    if "op" not in _ORACLE:
+        A, s, B = synth.split_state(7, (CHI,) * 4, CHI)
+        Dk, I, Da = CHI, CHI ** 3, CHI
+        As = A.reshape(Dk, I, Da) * s[None, None, :]
+        Bs = B.reshape(Da, Dk, I) * s[:, None, None]
+        _ORACLE["op"] = trg.SwapOp(As, Bs, None)
+        _ORACLE["cols"] = 1
+    op = _ORACLE["op"]
+    rows = op.shape[1]
+    cols = _ORACLE["cols"]
     while True:
-        om = synth.gaussian_matrix(3, Da * I, cols)
+        om = synth.gaussian_matrix(3, rows, cols)
         t = time.perf_counter()
         op.matmul(om)
         dt = time.perf_counter() - t
         if dt >= min_seconds or cols >= 3 * CHI:
             break
         cols = min(3 * CHI, max(cols * 2, int(cols * min_seconds / max(dt, 1e-3)) + 1))
+    _ORACLE["cols"] = cols
     sample_flops = 4.0 * CHI ** 6 * cols
     per_step = dt * step_flops(CHI, R, Q) / sample_flops
     desc = ("oracle SwapOp.matmul (Mid @ Omega of the chi=48 bond swap) on %d sketch columns: "
@@ -167,11 +176,12 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(min_seconds=2.0)
+        oracle_sample(min_seconds=min(2.0, args.sample_seconds))
     times = []
     desc, threads = "", os.cpu_count()
     for _ in range(args.steps):
-        per_step, desc, threads = oracle_sample(min_seconds=max(2.0, 20.0 / max(args.steps, 1)))
+        per_step, desc, threads = oracle_sample(
+            min_seconds=max(min(2.0, args.sample_seconds), args.sample_seconds / max(args.steps, 1)))
         times.append(per_step)
     per = sum(times) / len(times)
     value = 1.0 / per
@@ -347,6 +357,8 @@ def main():
     ap.add_argument("--chi", type=int, default=CHI,
                     help="bond dimension (48 is the benchmark; smaller values size ncu captures)")
     ap.add_argument("--r", type=int, default=R)
+    ap.add_argument("--sample-seconds", type=float, default=20.0,
+                    help="host seconds of oracle work the reference arm times (over all steps)")
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
