@@ -143,9 +143,12 @@ typedef struct {
   double flops[5];     /* algorithmic flops: swap, triad, squeeze, contract, resplit */
   double ms[5];        /* device time of each stage (CUDA events) */
   double swap_gap;     /* (sigma_{Dg-1} - sigma_Dg) / sigma_0 at the swap cut (inf if none) */
-  int tc_launches;     /* tcgen05 GEMM launches in the step */
+  int tc_launches;     /* tcgen05 GEMM launches of the step on the context's stream; the
+                          factorisations that run concurrently on worker streams (triad
+                          isometries, squeezer factors) are counted in kernel_launches only,
+                          since their event times include the GPU they share */
   int kernel_launches; /* all library kernel launches in the step */
-  double tc_ms;        /* device time of those launches (needs params.profile = 1) */
+  double tc_ms;        /* device time of the tc_launches (needs params.profile = 1) */
   double tc_flops;     /* their algorithmic flops, 2 M N K per contraction */
 } tatrg_step_info;
 

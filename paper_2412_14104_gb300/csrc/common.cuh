@@ -106,6 +106,8 @@ class DevBuf {
     p_ = nullptr;
     n_ = 0;
   }
+  // Free on stream s instead of the allocating stream (s must be ordered after every use).
+  void rebind(cudaStream_t s) { s_ = s; }
   template <class T> T* as() const { return reinterpret_cast<T*>(p_); }
   double* d() const { return reinterpret_cast<double*>(p_); }
   size_t bytes() const { return n_; }

@@ -7,6 +7,9 @@
 #include <atomic>
 #include <mutex>
 #include <thread>
+#include <functional>
+#include <exception>
+#include <memory>
 #include <string>
 
 #include "engine.cuh"
@@ -102,6 +105,23 @@ struct tatrg_ctx {
   tatrg_ctx(const tatrg_params& pp, cudaStream_t s) : p(pp), stream(s), eng(s) {
     eng.stats().timing = pp.profile != 0;
   }
+  ~tatrg_ctx() {
+    for (cudaStream_t w : side) {
+      cudaStreamSynchronize(w);
+      cudaStreamDestroy(w);
+    }
+  }
+
+  // Worker streams for the independent factorisations of one stage, and the launches of
+  // the engines that ran on them during the current step.
+  std::vector<cudaStream_t> side;
+  long side_launches = 0;
+  using Task = std::function<void(Engine&)>;
+  // Runs the tasks concurrently after the work queued so far on the context's stream, each
+  // on its own host thread, stream and engine (the precision of the context's engine); the
+  // context's stream then waits for all of them.  A task allocates its outputs on its own
+  // stream and rebinds them to the context's stream.  The first error is rethrown.
+  void concurrent(std::vector<Task>& tasks);
 
   int64_t chi() const { return p.chi; }
   int64_t width() const { return int64_t(p.r) * p.chi; }
@@ -130,12 +150,16 @@ struct tatrg_ctx {
   // tangents Xd, Yd (may be null) flip with them.
   void fix_sign_cols(double* X, int64_t F, int n, double* Y, int64_t F2, double* Xd = nullptr,
                      double* Yd = nullptr) {
-    DevBuf v(std::max(n, 1) * sizeof(double), stream);
-    weighted_colsum(X, F, n, v.d(), stream);
-    flip_by_sign(X, F, n, nullptr, 0, v.d(), stream);
-    if (Y) flip_by_sign(Y, F2, n, nullptr, 0, v.d(), stream);
-    if (Xd) flip_by_sign(Xd, F, n, nullptr, 0, v.d(), stream);
-    if (Yd) flip_by_sign(Yd, F2, n, nullptr, 0, v.d(), stream);
+    fix_sign_cols_on(stream, X, F, n, Y, F2, Xd, Yd);
+  }
+  static void fix_sign_cols_on(cudaStream_t st, double* X, int64_t F, int n, double* Y, int64_t F2,
+                               double* Xd = nullptr, double* Yd = nullptr) {
+    DevBuf v(std::max(n, 1) * sizeof(double), st);
+    weighted_colsum(X, F, n, v.d(), st);
+    flip_by_sign(X, F, n, nullptr, 0, v.d(), st);
+    if (Y) flip_by_sign(Y, F2, n, nullptr, 0, v.d(), st);
+    if (Xd) flip_by_sign(Xd, F, n, nullptr, 0, v.d(), st);
+    if (Yd) flip_by_sign(Yd, F2, n, nullptr, 0, v.d(), st);
   }
   // Same, but Y is n x F2 (flip its rows).
   void fix_sign_cols_rows(double* X, int64_t F, int n, double* Y, int64_t F2, double* Xd = nullptr,
@@ -159,9 +183,9 @@ struct tatrg_ctx {
                           DMat* psid = nullptr);
   double trace();
   double trace_tan(double tt);  // d ln tTr given tTr
-  DMat isometry(const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out,
+  DMat isometry(Engine& E, const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out,
                 const double* rhod = nullptr, DMat* Ud = nullptr);
-  void factor(const double* rho, int64_t P, int kind, DMat& Rt, const double* rhod = nullptr,
+  void factor(Engine& E, const double* rho, int64_t P, int kind, DMat& Rt, const double* rhod = nullptr,
               DMat* Rtd = nullptr);
 };
 
@@ -301,8 +325,9 @@ double tatrg_ctx::trace_tan(double tt) {
 
 // Leading eigenvectors of a PSD Gram (Eqs. 2-3): exact (k >= G) or RSVD with ell = k.
 // With rhod (tangent mode) also the tangent of U in *Ud (constant for ATRG).
-DMat tatrg_ctx::isometry(const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out,
+DMat tatrg_ctx::isometry(Engine& E, const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out,
                          const double* rhod, DMat* Ud) {
+  cudaStream_t stream = E.stream();
   DMat U;
   if (p.method == TATRG_ATRG) {
     U.buf = dalloc(Gd * Gd, stream);
@@ -323,17 +348,17 @@ DMat tatrg_ctx::isometry(const double* rho, int64_t Gd, int kind, std::vector<do
   SvdResult e;
   Engine::SvdTan et;
   if (k >= Gd) {
-    e = eng.svd(rho, Gd, Gd);
-    if (rhod) et = eng.svd_tan(rhod, Gd, Gd, e, keep_count(e.s, 1e-14, k), multiplet_groups(e.s, tau));
+    e = E.svd(rho, Gd, Gd);
+    if (rhod) et = E.svd_tan(rhod, Gd, Gd, e, keep_count(e.s, 1e-14, k), multiplet_groups(e.s, tau));
   } else {
     DevBuf om(Gd * k * sizeof(double), stream);
-    gaussian(p.seed, stream_id(step, kind), replica, Gd * k, om.d(), stream, eng.prec != 0);
+    gaussian(p.seed, stream_id(step, kind), replica, Gd * k, om.d(), stream, E.prec != 0);
     if (rhod) {
-      Engine::RsvdT r = eng.rsvd_psd_t(rho, rhod, Gd, k, p.q, om.d(), tau);
+      Engine::RsvdT r = E.rsvd_psd_t(rho, rhod, Gd, k, p.q, om.d(), tau);
       e = std::move(r.e);
       et = std::move(r.t);
     } else {
-      e = eng.rsvd_psd(rho, Gd, k, p.q, om.d());
+      e = E.rsvd_psd(rho, Gd, k, p.q, om.d());
     }
   }
   int keep = keep_count(e.s, 1e-14, k);
@@ -348,30 +373,31 @@ DMat tatrg_ctx::isometry(const double* rho, int64_t Gd, int kind, std::vector<do
     Ud->cols = keep;
     copy_modes(Ud->p(), et.U.p(), modes({{Gd, et.U.cols, keep}, {keep, 1, 1}}), 1.0, stream);
   }
-  fix_sign_cols(U.p(), Gd, keep, nullptr, 0, rhod ? Ud->p() : nullptr);
+  fix_sign_cols_on(stream, U.p(), Gd, keep, nullptr, 0, rhod ? Ud->p() : nullptr);
   if (lam_out) *lam_out = e.s;
   return U;
 }
 
 // rho ~= R^T R from the leading eigenpairs (exact when ell >= P); returns R^T (P x keep),
 // and with rhod its tangent in *Rtd: d(U sqrt(l)) = dU sqrt(l) + U dl / (2 sqrt(l)).
-void tatrg_ctx::factor(const double* rho, int64_t P, int kind, DMat& Rt, const double* rhod,
+void tatrg_ctx::factor(Engine& E, const double* rho, int64_t P, int kind, DMat& Rt, const double* rhod,
                        DMat* Rtd) {
+  cudaStream_t stream = E.stream();
   const int64_t ell = std::min(width(), P);
   SvdResult e;
   Engine::SvdTan et;
   if (ell >= P) {
-    e = eng.svd(rho, P, P);
-    if (rhod) et = eng.svd_tan(rhod, P, P, e, keep_count(e.s, 1e-14, ell), multiplet_groups(e.s, tau));
+    e = E.svd(rho, P, P);
+    if (rhod) et = E.svd_tan(rhod, P, P, e, keep_count(e.s, 1e-14, ell), multiplet_groups(e.s, tau));
   } else {
     DevBuf om(P * ell * sizeof(double), stream);
-    gaussian(p.seed, stream_id(step, kind), replica, P * ell, om.d(), stream, eng.prec != 0);
+    gaussian(p.seed, stream_id(step, kind), replica, P * ell, om.d(), stream, E.prec != 0);
     if (rhod) {
-      Engine::RsvdT r = eng.rsvd_psd_t(rho, rhod, P, ell, p.q, om.d(), tau);
+      Engine::RsvdT r = E.rsvd_psd_t(rho, rhod, P, ell, p.q, om.d(), tau);
       e = std::move(r.e);
       et = std::move(r.t);
     } else {
-      e = eng.rsvd_psd(rho, P, ell, p.q, om.d());
+      e = E.rsvd_psd(rho, P, ell, p.q, om.d());
     }
   }
   int keep = keep_count(e.s, 1e-14, ell);
@@ -387,7 +413,7 @@ void tatrg_ctx::factor(const double* rho, int64_t P, int kind, DMat& Rt, const d
   if (rhod) {
     std::vector<double> dsq(keep);
     for (int i = 0; i < keep; ++i) dsq[i] = et.s[i] / (2.0 * sq[i]);
-    DevBuf dsqd = eng.upload(dsq);
+    DevBuf dsqd = E.upload(dsq);
     Rtd->buf = dalloc(P * keep, stream);
     Rtd->rows = P;
     Rtd->cols = keep;
@@ -397,6 +423,50 @@ void tatrg_ctx::factor(const double* rho, int64_t P, int kind, DMat& Rt, const d
     scale_axis(Rt.p(), sqd.d(), P, keep, 1, 1, stream);
   }
   TATRG_CUDA(cudaStreamSynchronize(stream));
+}
+
+void tatrg_ctx::concurrent(std::vector<Task>& tasks) {
+  const size_t n = tasks.size();
+  while (side.size() < n) {
+    cudaStream_t w;
+    TATRG_CUDA(cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking));
+    side.push_back(w);
+  }
+  cudaEvent_t ready;
+  TATRG_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  TATRG_CUDA(cudaEventRecord(ready, stream));
+  std::vector<std::exception_ptr> err(n);
+  std::vector<std::unique_ptr<Engine>> engines(n);
+  std::vector<std::thread> threads;
+  for (size_t i = 0; i < n; ++i) {
+    threads.emplace_back([&, i]() {
+      try {
+        TATRG_CUDA(cudaStreamWaitEvent(side[i], ready, 0));
+        engines[i] = std::make_unique<Engine>(side[i]);
+        Engine& e = *engines[i];
+        e.prec = eng.prec;
+        e.allow_tc = eng.allow_tc;
+        e.stats().timing = eng.stats().timing;
+        tasks[i](e);
+      } catch (...) {
+        err[i] = std::current_exception();
+      }
+    });
+  }
+  for (auto& t : threads) t.join();
+  for (size_t i = 0; i < n; ++i) {
+    cudaEvent_t done;
+    TATRG_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    TATRG_CUDA(cudaEventRecord(done, side[i]));
+    TATRG_CUDA(cudaStreamWaitEvent(stream, done, 0));
+    TATRG_CUDA(cudaEventDestroy(done));
+    if (engines[i]) {
+      side_launches += engines[i]->stats().launches;
+    }
+  }
+  TATRG_CUDA(cudaEventDestroy(ready));
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
 }
 
 namespace {
@@ -426,6 +496,7 @@ void tatrg_ctx::rg_step() {
   const long launches0 = eng.stats().launches, tc0 = eng.stats().tc_launches;
   const double tcf0 = eng.stats().flops_tc;
   eng.stats().drain_ms();
+  side_launches = 0;
   for (auto& f : flops) f = 0.0;
   auto count = [&](Stage sg, const GemmDesc& g) {
     flops[sg] += 2.0 * double(g.m.total()) * double(g.n.total()) * double(g.k.total());
@@ -729,10 +800,25 @@ void tatrg_ctx::rg_step() {
   Xsd.release();
   Ysd.release();
   DMat UAd, UXd, UYd, UDd;
-  DMat UA = isometry(rho_a.d(), Gd, KIND_TRIAD_A, nullptr, tp(rho_ad), &UAd);
-  DMat UX = isometry(rho_x.d(), Gd, KIND_TRIAD_X, nullptr, tp(rho_xd), &UXd);
-  DMat UY = isometry(rho_y.d(), Gd, KIND_TRIAD_Y, nullptr, tp(rho_yd), &UYd);
-  DMat UD = isometry(rho_d.d(), Gd, KIND_TRIAD_D, nullptr, tp(rho_dd), &UDd);
+  DMat UA, UX, UY, UD;
+  if (!T) {
+    // the four isometries are independent: factorise the Grams concurrently
+    std::vector<Task> tasks;
+    const double* rhos[4] = {rho_a.d(), rho_x.d(), rho_y.d(), rho_d.d()};
+    DMat* outs[4] = {&UA, &UX, &UY, &UD};
+    const int kinds[4] = {KIND_TRIAD_A, KIND_TRIAD_X, KIND_TRIAD_Y, KIND_TRIAD_D};
+    for (int i = 0; i < 4; ++i)
+      tasks.push_back([&, i](Engine& E) {
+        *outs[i] = isometry(E, rhos[i], Gd, kinds[i], nullptr);
+        outs[i]->buf.rebind(st);
+      });
+    concurrent(tasks);
+  } else {
+    UA = isometry(eng, rho_a.d(), Gd, KIND_TRIAD_A, nullptr, tp(rho_ad), &UAd);
+    UX = isometry(eng, rho_x.d(), Gd, KIND_TRIAD_X, nullptr, tp(rho_xd), &UXd);
+    UY = isometry(eng, rho_y.d(), Gd, KIND_TRIAD_Y, nullptr, tp(rho_yd), &UYd);
+    UD = isometry(eng, rho_d.d(), Gd, KIND_TRIAD_D, nullptr, tp(rho_dd), &UDd);
+  }
   const int64_t KA = UA.cols, KX = UX.cols, KY = UY.cols, KD = UD.cols;
   // E[i0,kA,s,a] = sum_G A[i0,G,s,a] UA[G,kA]
   DevBuf E(D0 * KA * Ds * Da_ * sizeof(double), st), F(Da_ * KX * Ds * Dg * sizeof(double), st),
@@ -917,12 +1003,37 @@ void tatrg_ctx::rg_step() {
              t2.d(), tp(t2d), ll.d(), tp(lld), rhoR[nu - 1].d(), tp(rhoRd[nu - 1]));
       }
     }
+    // square-root factors of the 2(d - 1) Grams; without tangents they are independent and
+    // run concurrently
+    std::vector<DMat> RtLs(d - 1), RtRs(d - 1), RtLds(d - 1), RtRds(d - 1);
+    if (!T) {
+      std::vector<Task> tasks;
+      for (int nu = 1; nu <= d - 1; ++nu) {
+        const int64_t Pn = D[nu] * D[nu];
+        tasks.push_back([&, nu, Pn](Engine& E) {
+          factor(E, rhoL[nu - 1].d(), Pn, KIND_SQ_LEFT + nu - 1, RtLs[nu - 1]);
+          RtLs[nu - 1].buf.rebind(st);
+        });
+        tasks.push_back([&, nu, Pn](Engine& E) {
+          factor(E, rhoR[nu - 1].d(), Pn, KIND_SQ_RIGHT + nu - 1, RtRs[nu - 1]);
+          RtRs[nu - 1].buf.rebind(st);
+        });
+      }
+      concurrent(tasks);
+    } else {
+      for (int nu = 1; nu <= d - 1; ++nu) {
+        const int64_t Pn = D[nu] * D[nu];
+        factor(eng, rhoL[nu - 1].d(), Pn, KIND_SQ_LEFT + nu - 1, RtLs[nu - 1], tp(rhoLd[nu - 1]), &RtLds[nu - 1]);
+        factor(eng, rhoR[nu - 1].d(), Pn, KIND_SQ_RIGHT + nu - 1, RtRs[nu - 1], tp(rhoRd[nu - 1]), &RtRds[nu - 1]);
+      }
+    }
     // oblique projectors: C = R_L R_R^T = U S V^T, M = R_R^T V_k S^-1/2, N = S^-1/2 U_k^T R_L
     for (int nu = 1; nu <= d - 1; ++nu) {
       const int64_t Dn = D[nu], Pn = Dn * Dn;
-      DMat RtL, RtR, RtLd, RtRd;
-      factor(rhoL[nu - 1].d(), Pn, KIND_SQ_LEFT + nu - 1, RtL, tp(rhoLd[nu - 1]), &RtLd);
-      factor(rhoR[nu - 1].d(), Pn, KIND_SQ_RIGHT + nu - 1, RtR, tp(rhoRd[nu - 1]), &RtRd);
+      DMat& RtL = RtLs[nu - 1];
+      DMat& RtR = RtRs[nu - 1];
+      DMat& RtLd = RtLds[nu - 1];
+      DMat& RtRd = RtRds[nu - 1];
       const int64_t kL = RtL.cols, kR = RtR.cols;
       DevBuf C(kL * kR * sizeof(double), st);
       eng.mm(kL, kR, Pn, RtL.p(), kL, true, RtR.p(), kR, false, C.d(), kR);
@@ -1132,7 +1243,9 @@ void tatrg_ctx::rg_step() {
   for (int i = 0; i < d && i < 4; ++i) info.dims[i] = int(D[i]);
   info.dims[4] = int(Da);
   info.lnc = lnc.back();
-  info.kernel_launches = int(eng.stats().launches - launches0);
+  // tensor-core figures of the context's own stream: the factorisations on the worker
+  // streams share the GPU with one another, so their event times are not kernel times
+  info.kernel_launches = int(eng.stats().launches - launches0 + side_launches);
   info.tc_launches = int(eng.stats().tc_launches - tc0);
   info.tc_flops = eng.stats().flops_tc - tcf0;
   info.tc_ms = eng.stats().drain_ms();
