@@ -1,7 +1,7 @@
 // Split-precision contractions on the 5th-generation tensor cores (sm_103a).
 //
 // A float64 operand x is split into two tensor-core numbers, x = hi + lo + O(2^-22 |x|)
-// for TF32 (hi = tf32(x), lo = tf32(x - hi)) or O(2^-16 |x|) for BF16, and
+// for TF32 (f = float(x), hi = tf32(f), lo = tf32(f - hi)) or O(2^-16 |x|) for BF16, and
 // A B ~= A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 in tensor memory
 // ("3xTF32" / "BF16x3").  Flow per contraction:
 //   pack   : gather the multi-mode operand into a K-major, zero-padded [rows][K] panel of
@@ -24,7 +24,6 @@
 namespace tatrg {
 namespace {
 
-// stages (64-byte K slices) accumulated in one FP32 chain before a drain
 // bytes of K per shared-memory stage row: one SWIZZLE_64B or SWIZZLE_128B atom row
 #ifndef TATRG_KSLICE
 #define TATRG_KSLICE 128
@@ -39,7 +38,7 @@ constexpr int TC_BN = 128;
 constexpr int KSLICE = TATRG_KSLICE;
 static_assert(KSLICE == 64 || KSLICE == 128, "stage rows are one 64- or 128-byte swizzle atom");
 constexpr int SMEM_BUDGET = 192 * 1024;
-constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s; a CTA gives up after 4 WAIT_NS
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s: the bound of every mbarrier wait
 
 __device__ int g_tc_error;
 
