@@ -1,7 +1,8 @@
-// Small dense FP64 linear algebra, one thread block per problem: Cholesky (the core of
-// CholeskyQR2), inverse of the triangular factor, and the one-sided (Hestenes) Jacobi SVD
-// used for every core SVD / PSD eigenproblem of the RG step (swap core, triad Gram
-// eigenvectors, squeezer factors and core, re-split).
+// Small dense FP64 linear algebra: Cholesky (the core of CholeskyQR2; one block), the
+// inverse of the triangular factor (one warp per column), and the one-sided (Hestenes)
+// Jacobi SVD used for every core SVD / PSD eigenproblem of the RG step (swap core, triad
+// Gram eigenvectors, squeezer factors and core, re-split): one block in shared memory for
+// small problems, otherwise one cooperative grid with a block per column pair.
 
 #include "kernels.cuh"
 
@@ -553,8 +554,9 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
     jacobi_kernel<<<1, threads, size_t(m * N) * sizeof(double), s>>>(ac.d(), m, N, vc.d(), 60, tol, status_dev);
     TATRG_CUDA(cudaGetLastError());
   } else {
-    // tall: one block per pair and one launch per round; the host reads the rotation flag
-    // once per sweep.
+    // one block per column pair, all sweeps in one cooperative launch (its blocks are
+    // co-resident by construction; the barrier between rounds gives up after 2 s and
+    // reports status 2)
     DevBuf aux(4 * sizeof(double), s);
     double* fro2 = aux.d();
     int* rot = reinterpret_cast<int*>(aux.d() + 1);
@@ -562,8 +564,6 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
     TATRG_CUDA(cudaMemsetAsync(aux.d(), 0, 4 * sizeof(double), s));
     sumsq_kernel<<<int(std::min<int64_t>(cdiv(m * N, 256), 1024)), 256, 0, s>>>(ac.d(), m * N, fro2);
     TATRG_CUDA(cudaGetLastError());
-    // all sweeps in one cooperative launch (its blocks are co-resident by construction; the
-    // barrier between rounds still gives up after 2 s and reports status 2)
     int thr = m >= 256 ? 256 : (m >= 128 ? 128 : 64);
     int dev = 0, sms = 0, per_sm = 0;
     TATRG_CUDA(cudaGetDevice(&dev));
