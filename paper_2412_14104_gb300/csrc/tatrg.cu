@@ -438,20 +438,25 @@ void tatrg_ctx::concurrent(std::vector<Task>& tasks) {
   std::vector<std::exception_ptr> err(n);
   std::vector<std::unique_ptr<Engine>> engines(n);
   std::vector<std::thread> threads;
+  auto work = [&](size_t i) {
+    try {
+      TATRG_CUDA(cudaStreamWaitEvent(side[i], ready, 0));
+      engines[i] = std::make_unique<Engine>(side[i]);
+      Engine& e = *engines[i];
+      e.prec = eng.prec;
+      e.allow_tc = eng.allow_tc;
+      e.stats().timing = eng.stats().timing;
+      tasks[i](e);
+    } catch (...) {
+      err[i] = std::current_exception();
+    }
+  };
   for (size_t i = 0; i < n; ++i) {
-    threads.emplace_back([&, i]() {
-      try {
-        TATRG_CUDA(cudaStreamWaitEvent(side[i], ready, 0));
-        engines[i] = std::make_unique<Engine>(side[i]);
-        Engine& e = *engines[i];
-        e.prec = eng.prec;
-        e.allow_tc = eng.allow_tc;
-        e.stats().timing = eng.stats().timing;
-        tasks[i](e);
-      } catch (...) {
-        err[i] = std::current_exception();
-      }
-    });
+    try {
+      threads.emplace_back(work, i);
+    } catch (...) {  // no thread: run the task here
+      work(i);
+    }
   }
   for (auto& t : threads) t.join();
   for (size_t i = 0; i < n; ++i) {
@@ -460,9 +465,7 @@ void tatrg_ctx::concurrent(std::vector<Task>& tasks) {
     TATRG_CUDA(cudaEventRecord(done, side[i]));
     TATRG_CUDA(cudaStreamWaitEvent(stream, done, 0));
     TATRG_CUDA(cudaEventDestroy(done));
-    if (engines[i]) {
-      side_launches += engines[i]->stats().launches;
-    }
+    if (engines[i]) side_launches += engines[i]->stats().launches;
   }
   TATRG_CUDA(cudaEventDestroy(ready));
   for (auto& e : err)
