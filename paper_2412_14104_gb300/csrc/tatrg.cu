@@ -1666,6 +1666,7 @@ tatrg_status tatrg_orth(int precision, int64_t m, int64_t n, const double* Y, do
                         int* k, void* stream) {
   return guard(nullptr, [&] {
     TATRG_CHECK(Y && Q && R && k && m >= n && n >= 1 && n <= 1024, TATRG_EINVAL, "tatrg_orth: bad argument");
+    TATRG_CHECK(precision >= 0 && precision <= 2, TATRG_EINVAL, "tatrg_orth: bad precision");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Engine e(s);
     e.prec = precision;

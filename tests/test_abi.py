@@ -42,3 +42,29 @@ def test_bad_arguments_fail_without_a_gpu(libpath):
     assert L.tatrg_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert b"chi" in L.tatrg_last_error(None)
     assert L.tatrg_rg_step(None, 1) == 1
+
+
+def test_building_blocks_reject_bad_sizes_before_touching_memory(libpath):
+    """Argument checks of the device building blocks run on the host before any launch or
+    copy, so they can be exercised here with placeholder pointers."""
+    import paper_2412_14104_gb300 as tg
+    L = tg.lib()
+    fake = ctypes.c_void_p(256)  # never dereferenced: every call below fails its checks first
+    k = ctypes.c_int(0)
+    # contraction: an extent of 0, a precision out of range
+    c = tg._contraction([(0, 1, 1)], [(4, 1, 1)], [(4, 1, 1)], 1.0, 0.0)
+    assert L.tatrg_contract(ctypes.byref(c), 0, fake, fake, fake, None) == 1
+    c = tg._contraction([(4, 4, 4)], [(4, 1, 1)], [(4, 1, 4)], 1.0, 0.0)
+    assert L.tatrg_contract(ctypes.byref(c), 3, fake, fake, fake, None) == 1
+    assert L.tatrg_contract(ctypes.byref(c), 0, None, fake, fake, None) == 1
+    # the generated-sketch contraction exists for the split precisions only
+    assert L.tatrg_contract_sketch(ctypes.byref(c), 0, fake, 1, 2, 0, fake, None) == 1
+    assert b"split precision" in L.tatrg_last_error(None)
+    # SVD and orthonormalisation need m >= n and 1 <= n <= 1024
+    assert L.tatrg_svd(3, 4, fake, fake, fake, fake, None) == 1
+    assert L.tatrg_svd(5000, 1025, fake, fake, fake, fake, None) == 1
+    assert L.tatrg_svd_noalloc(3, 4, fake, fake, fake, fake, None) == 1
+    assert L.tatrg_orth(0, 3, 4, fake, fake, fake, ctypes.byref(k), None) == 1
+    assert L.tatrg_orth(9, 8, 4, fake, fake, fake, ctypes.byref(k), None) == 1
+    # sketches: negative sizes
+    assert L.tatrg_gaussian(1, 2, 0, -1, 4, fake, None) == 1
