@@ -370,3 +370,40 @@ def test_derivative_onsager_2d():
     exact = (exact_ising.onsager_lnz(beta + e) - exact_ising.onsager_lnz(beta - e)) / (2 * e)
     got = derivatives.dlnz_dbeta(beta, 0.0, 2, trg.Params(16, 3, q=2, seed=7), 40)
     assert abs(got - exact) < 1e-6, (got, exact)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_squeezers_are_optimal_oblique_projectors(seed):
+    """Eq. 5: the squeezer pair (M, N) built from the Grams rho_L = R_L^T R_L and
+    rho_R = R_R^T R_R is an oblique projector (N M = 1_k) whose error
+    || R_L (1 - M N) R_R^T ||_F^2 equals the sum of the discarded squared singular values of
+    C = R_L R_R^T, the Eckart-Young minimum over every rank-k product.  Square-root
+    factors here come from numpy's eigh, independently of the oracle's; the error does not
+    depend on that choice."""
+    rng = np.random.default_rng(seed)
+    D, k = 4, 5
+    P = D * D
+
+    def psd():
+        q, _ = np.linalg.qr(rng.standard_normal((P, P)))
+        return (q * (0.6 ** np.arange(P))) @ q.T
+
+    rho_l, rho_r = psd(), psd()
+    p = trg.Params(k, 4, q=2, seed=seed)  # width r chi = 20 >= P: exact factors
+    Ms, Ns = trg.squeezers([rho_l], [rho_r], p, step=1)
+    M = Ms[0].reshape(P, -1)
+    N = Ns[0].reshape(-1, P)
+    assert M.shape == (P, k) and N.shape == (k, P)
+    assert np.allclose(N @ M, np.eye(k), atol=1e-10)
+
+    def root(rho):
+        w, v = np.linalg.eigh(rho)
+        return np.sqrt(np.clip(w, 0.0, None))[:, None] * v.T
+
+    RL, RR = root(rho_l), root(rho_r)
+    S = np.linalg.svd(RL @ RR.T, compute_uv=False)
+    err = np.linalg.norm(RL @ (np.eye(P) - M @ N) @ RR.T) ** 2
+    assert abs(err - np.sum(S[k:] ** 2)) < 1e-10 * np.sum(S ** 2)
+    # any other rank-k oblique pair does worse, e.g. the orthogonal projector on M's range
+    Pm = M @ np.linalg.pinv(M)
+    assert np.linalg.norm(RL @ (np.eye(P) - Pm) @ RR.T) ** 2 >= err * (1 - 1e-12)
