@@ -407,3 +407,26 @@ def test_squeezers_are_optimal_oblique_projectors(seed):
     # any other rank-k oblique pair does worse, e.g. the orthogonal projector on M's range
     Pm = M @ np.linalg.pinv(M)
     assert np.linalg.norm(RL @ (np.eye(P) - Pm) @ RR.T) ** 2 >= err * (1 - 1e-12)
+
+
+def test_resplit_reproduces_the_product_and_rotates_the_legs():
+    """The re-split (A1): without truncation c A' diag(s') B' equals Phi Psi^T over the new
+    bond, with s' of unit 2-norm, orthonormal columns of A' and rows of B', and every leg
+    moved one position left (the next direction comes first)."""
+    rng = np.random.default_rng(8)
+    legs, Dg = (3, 2, 4), 5
+    phi = rng.standard_normal(legs + (Dg,))
+    psi = rng.standard_normal(legs + (Dg,))
+    p = trg.Params(64, 2, seed=1)
+    A, s, B, c = trg.resplit(phi, psi, p)
+    assert abs(np.linalg.norm(s) - 1.0) < 1e-14 and np.all(np.diff(s) <= 0)
+    Da = s.size
+    assert A.shape == (2, 4, 3, Da) and B.shape == (Da, 2, 4, 3)
+    am = A.reshape(-1, Da)
+    bm = B.reshape(Da, -1)
+    assert np.allclose(am.T @ am, np.eye(Da), atol=1e-13)
+    assert np.allclose(bm @ bm.T, np.eye(Da), atol=1e-13)
+    got = c * np.einsum("xyza,a,auvw->xyzuvw", A, s, B)
+    full = np.einsum("ijkg,lmng->ijklmn", phi, psi)
+    want = np.transpose(full, (1, 2, 0, 4, 5, 3))  # rotate forward and backward legs left
+    assert np.allclose(got, want, atol=1e-12 * np.abs(want).max())
