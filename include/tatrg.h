@@ -84,7 +84,11 @@ tatrg_status tatrg_init_ising(tatrg_ctx* ctx, double beta, double h, int d);
 /* Run `nsteps` coarse-graining steps (Sec. 2, Eqs. 1-7).  Each step halves the lattice
  * along the leg at position 0, normalises the new tensor by c_k = ||s'||_2 and adds
  * 2^-k ln c_k to the accumulator.  Returns after the last step's small host reads
- * (spectra needed for the rank cuts), so the call synchronises the stream. */
+ * (spectra needed for the rank cuts), so the call synchronises the stream.  Inside a
+ * step the independent factorisations of the triad isometries (Eqs. 2-3) and of the
+ * squeezer Grams (Eq. 5) run on short-lived host threads, each on a worker stream the
+ * context owns; they start after the work already queued on the context's stream and the
+ * context's stream waits for them, so the call keeps the stream semantics above. */
 tatrg_status tatrg_rg_step(tatrg_ctx* ctx, int nsteps);
 
 /* ln Z / V after the steps run so far: sum_k 2^-k ln c_k + 2^-N ln tTr T_N, where tTr
