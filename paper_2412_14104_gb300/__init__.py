@@ -227,16 +227,7 @@ def contract_sketch(m, n, k, A, seed, stream_id, C, replica=0, alpha=1.0, beta=0
 def contract(m, n, k, A, B, C, alpha=1.0, beta=0.0, precision=FP64, stream=None):
     """C[m, n] = alpha sum_k A[m, k] B[k, n] + beta C; m = [(ext, strideA, strideC), ...],
     n = [(ext, strideB, strideC), ...], k = [(ext, strideA, strideB), ...] (outermost first)."""
-    c = Contraction()
-    for name, modes in (("m", m), ("n", n), ("k", k)):
-        assert len(modes) <= 4
-        full = list(modes) + [(1, 0, 0)] * (4 - len(modes))
-        s1, s2 = {"m": ("m_sA", "m_sC"), "n": ("n_sB", "n_sC"), "k": ("k_sA", "k_sB")}[name]
-        for i, (e, a, b) in enumerate(full):
-            getattr(c, name + "_ext")[i] = e
-            getattr(c, s1)[i] = a
-            getattr(c, s2)[i] = b
-    c.alpha, c.beta = alpha, beta
+    c = _contraction(m, n, k, alpha, beta)
     _check(lib().tatrg_contract(ctypes.byref(c), precision, ctypes.c_void_p(A.data_ptr()),
                                 ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
                                 _stream_ptr(stream)))
