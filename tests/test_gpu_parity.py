@@ -56,9 +56,17 @@ def test_full_run_matches_oracle(name):
     on rounding; the strict tolerance then relaxes to 1e-7 for the rest of the run.
     Rounding differences grow by ~1.6 per step along the RG trajectory (measured with the
     oracle under a 1e-10 perturbation), so the per-step bound grows by that factor after
-    step 15; ln Z, where step k weighs 2^-k, keeps the 1e-11 bar."""
+    step 15; where the oracle's own rounding envelope (make_envelope.py: the spread of
+    its runs under relative 2^-50 noise on the initial split) is wider, 100 times the
+    envelope bounds the step instead.  ln Z, where step k weighs 2^-k, keeps the 1e-11
+    bar."""
     g = _gold(name)
     c = g["config"]
+    env = None
+    env_path = os.path.join(GOLD, "oracle_%s_envelope.json" % name)
+    if os.path.exists(env_path):
+        with open(env_path) as f:
+            env = json.load(f)
     ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"]).init_ising(c["beta"], c["h"], c["d"])
     tol = 1e-11
     for k in range(c["steps"]):
@@ -67,10 +75,15 @@ def test_full_run_matches_oracle(name):
             tol = 1e-7
         info = ctx.step_info()
         ltol = tol * 1.6 ** max(0, k - 15)
+        stol = 10 * ltol
+        if env is not None:
+            # never tighter than the oracle's own spread under rounding-level noise (x100)
+            ltol = max(ltol, 100.0 * env["env_lnc"][k + 1])
+            if env["env_s"][k + 1] is not None:
+                stol = max(stol, 100.0 * env["env_s"][k + 1])
         assert abs(info.lnc - g["lnc"][k + 1]) < ltol * max(1.0, abs(g["lnc"][k + 1])), k
         s = ctx.spectrum(0)
         assert s.size == len(g["s"][k + 1])
-        stol = 10 * ltol
         assert np.max(np.abs(s - np.array(g["s"][k + 1]))) < stol, k
     lnz = ctx.lnZ()
     assert abs(lnz - g["lnz"]) < tol * abs(g["lnz"])
