@@ -430,3 +430,33 @@ def test_resplit_reproduces_the_product_and_rotates_the_legs():
     full = np.einsum("ijkg,lmng->ijklmn", phi, psi)
     want = np.transpose(full, (1, 2, 0, 4, 5, 3))  # rotate forward and backward legs left
     assert np.allclose(got, want, atol=1e-12 * np.abs(want).max())
+
+
+def test_squeezer_grams_equal_dense_unit_cell_grams():
+    """Eq. 5 inputs: the Grams rho_L, rho_R that the oracle contracts through the triad
+    factors and the Xi / Omega environments equal the Grams of the dense two-site cell
+    Gamma = A X sigma Y^T D over each forward pair (i_nu(n+1^), i_nu(n)) and backward pair,
+    with every other leg summed.  Exact triad (r chi above every dimension), a random
+    state with unequal leg dimensions, so a swapped pair or a wrong leg fails."""
+    from paper_2412_14104_gb300 import synth
+    A, s, B = synth.split_state(4, (2, 2, 3, 2), 3)
+    p = trg.Params(64, 64, seed=5)
+    X, sig, Y = trg.bond_swap(A, s, B, p, 1)
+    E, F, G, H, I, J, K, L = trg.triad(A, B, X, sig, Y, p, 1)
+    rho_l, rho_r = trg.squeezer_grams(E, F, G, H, I, J, K, L, 2)
+    fwd = np.einsum("iabsx,xcdtg,g->iabscdtg", A, X, sig)
+    bwd = np.einsum("ybcdg,jefhy->bcdgjefh", Y, np.moveaxis(B, 0, -1))
+    gam = np.einsum("iabscdtg,BCDgjefh->iabscdtBCDjefh", fwd, bwd)
+    legs = "iabscdtBCDjefh"
+
+    def gram(pair):
+        rest = [x for x in legs if x not in pair]
+        g = np.transpose(gam, [legs.index(pair[0]), legs.index(pair[1])] + [legs.index(x) for x in rest])
+        m = g.reshape(g.shape[0] * g.shape[1], -1)
+        return m @ m.T
+
+    for nu, (fp, bp) in enumerate((("ac", "Be"), ("bd", "Cf"), ("st", "Dh"))):
+        dl, dr = gram(fp), gram(bp)
+        assert np.allclose(rho_l[nu], dl, atol=1e-13 * np.abs(dl).max()), nu
+        assert np.allclose(rho_r[nu], dr, atol=1e-13 * np.abs(dr).max()), nu
+        assert not np.allclose(rho_l[nu], gram(fp[::-1]), atol=1e-3 * np.abs(dl).max())
