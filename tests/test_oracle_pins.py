@@ -460,3 +460,24 @@ def test_squeezer_grams_equal_dense_unit_cell_grams():
         assert np.allclose(rho_l[nu], dl, atol=1e-13 * np.abs(dl).max()), nu
         assert np.allclose(rho_r[nu], dr, atol=1e-13 * np.abs(dr).max()), nu
         assert not np.allclose(rho_l[nu], gram(fp[::-1]), atol=1e-3 * np.abs(dl).max())
+
+
+def test_contraction_equals_dense_cell_with_squeezers():
+    """Eqs. 6-7: Phi Psi^T from the factored chain C1-C4 equals the dense two-site cell
+    A X sigma Y^T D with the squeezers M (forward pairs) and N (backward pairs) attached,
+    in the exact-triad regime, for a random state with unequal leg dimensions."""
+    from paper_2412_14104_gb300 import synth
+    A, s, B = synth.split_state(4, (2, 2, 3, 2), 3)
+    p = trg.Params(64, 64, seed=5)
+    X, sig, Y = trg.bond_swap(A, s, B, p, 1)
+    E, F, G, H, I, J, K, L = trg.triad(A, B, X, sig, Y, p, 1)
+    rho_l, rho_r = trg.squeezer_grams(E, F, G, H, I, J, K, L, 2)
+    Ms, Ns = trg.squeezers(rho_l, rho_r, p, 1)
+    phi, psi = trg.contract(E, F, G, H, I, J, K, L, Ms, Ns, 2)
+    got = np.einsum("iuvzg,jUVZg->iuvzjUVZ", phi, psi)
+    fwd = np.einsum("iabsx,xcdtg,g->iabscdtg", A, X, sig)
+    bwd = np.einsum("ybcdg,jefhy->bcdgjefh", Y, np.moveaxis(B, 0, -1))
+    gam = np.einsum("iabscdtg,BCDgjefh->iabscdtBCDjefh", fwd, bwd)
+    want = np.einsum("iabscdtBCDjefh,acu,bdv,stz,UBe,VCf,ZDh->iuvzjUVZ", gam, Ms[0], Ms[1], Ms[2],
+                     Ns[0], Ns[1], Ns[2], optimize=True)
+    assert np.allclose(got, want, atol=1e-13 * np.abs(want).max())
