@@ -481,3 +481,19 @@ def test_contraction_equals_dense_cell_with_squeezers():
     want = np.einsum("iabscdtBCDjefh,acu,bdv,stz,UBe,VCf,ZDh->iuvzjUVZ", gam, Ms[0], Ms[1], Ms[2],
                      Ns[0], Ns[1], Ns[2], optimize=True)
     assert np.allclose(got, want, atol=1e-13 * np.abs(want).max())
+
+
+def test_bond_swap_preserves_the_two_site_product():
+    """Eq. 1: without truncation A (X sigma Y^T) D equals the dense product of two site
+    tensors T = A s B joined along the active direction (the upper site's backward leg 0
+    with the lower site's forward leg 0), for a random state with unequal leg dimensions."""
+    from paper_2412_14104_gb300 import synth
+    A, s, B = synth.split_state(4, (2, 2, 3, 2), 3)
+    p = trg.Params(64, 64, seed=5)
+    X, sig, Y = trg.bond_swap(A, s, B, p, 1)
+    fwd = np.einsum("iabsx,xcdtg,g->iabscdtg", A, X, sig)
+    bwd = np.einsum("ybcdg,jefhy->bcdgjefh", Y, np.moveaxis(B, 0, -1))
+    got = np.einsum("iabscdtg,BCDgjefh->iabscdtBCDjefh", fwd, bwd)
+    T = np.einsum("iabsx,x,xjefh->iabsjefh", A, s, B)
+    want = np.einsum("iabskBCD,kcdtjefh->iabscdtBCDjefh", T, T)
+    assert np.allclose(got, want, atol=1e-13 * np.abs(want).max())
