@@ -31,6 +31,7 @@ sys.path.insert(0, ROOT)
 CHI, R, Q, BETA, H, SEED = 48, 3, 2, 0.1497, 1e-4, 2
 WORKLOAD = ("4D Ising Triad-ATRG, chi=48 r=3 q=2, beta=0.1497 h=1e-4, seed 2; one "
             "steady-state RG step (legs 48^4, bond 48)")
+METRIC = "RG steps/s at chi=48 (split precision); TFLOP/s; df vs FP64 oracle"
 
 
 def step_flops(chi, r, q):
@@ -129,15 +130,35 @@ def barrier(world):
 
 
 # --------------------------------------------------------------------------------------
-_ORACLE = {}  # the chi = 48 swap operator and sketch width, built once per process
+_ORACLE = {}  # the chi = 48 swap operator, built once per process
+SAMPLE_COLS = 8  # sketch columns of the timed oracle sample (the same in every leg)
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((d.get("num_threads", 0) for d in threadpool_info()), default=os.cpu_count())
+    except Exception:
+        return int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count()))
 
 
 def oracle_sample(min_seconds=10.0):
-    """Time the FP64 oracle's bond-swap operator (one product Mid @ Omega of the chi = 48
-    step) on a number of sketch columns that takes ~min_seconds; return (seconds per RG
-    step extrapolated by flops, description, threads).  Building the state and drawing the
-    sketch are not timed."""
-    import numpy as np
+    """Time the FP64 oracle's bond-swap operator on the chi = 48 state: products
+    Mid @ Omega (the first product of the Eq. 1 randomized SVD) with SAMPLE_COLS sketch
+    columns, repeated until min_seconds have passed.  Returns (seconds per RG step scaled by
+    the step's algorithmic flops, description, BLAS threads).  Building the state and the
+    sketch is not timed."""
     from oracle import trg
     from paper_2412_14104_gb300 import synth
     if "op" not in _ORACLE:
@@ -146,53 +167,65 @@ def oracle_sample(min_seconds=10.0):
         As = A.reshape(Dk, I, Da) * s[None, None, :]
         Bs = B.reshape(Da, Dk, I) * s[:, None, None]
         _ORACLE["op"] = trg.SwapOp(As, Bs, None)
-        _ORACLE["cols"] = 1
-    op = _ORACLE["op"]
-    rows = op.shape[1]
-    cols = _ORACLE["cols"]
-    while True:
-        om = synth.gaussian_matrix(3, rows, cols)
+        _ORACLE["om"] = synth.gaussian_matrix(3, _ORACLE["op"].shape[1], SAMPLE_COLS)
+    op, om = _ORACLE["op"], _ORACLE["om"]
+    reps, dt = 0, 0.0
+    while dt < min_seconds or reps == 0:
         t = time.perf_counter()
         op.matmul(om)
-        dt = time.perf_counter() - t
-        if dt >= min_seconds or cols >= 3 * CHI:
-            break
-        cols = min(3 * CHI, max(cols * 2, int(cols * min_seconds / max(dt, 1e-3)) + 1))
-    _ORACLE["cols"] = cols
-    sample_flops = 4.0 * CHI ** 6 * cols
+        dt += time.perf_counter() - t
+        reps += 1
+    sample_flops = 4.0 * CHI ** 6 * SAMPLE_COLS * reps
     per_step = dt * step_flops(CHI, R, Q) / sample_flops
-    desc = ("oracle SwapOp.matmul (Mid @ Omega of the chi=48 bond swap) on %d sketch columns: "
-            "%.3g flop in %.2f s, scaled by the step's %.3g algorithmic flop" %
-            (cols, sample_flops, dt, step_flops(CHI, R, Q)))
+    desc = ("oracle SwapOp.matmul (Mid @ Omega of the chi=48 bond swap, %d sketch columns) x %d: "
+            "%.3g flop in %.2f s, scaled to one RG step by its %.3g algorithmic flop" %
+            (SAMPLE_COLS, reps, sample_flops, dt, step_flops(CHI, R, Q)))
+    return per_step, desc, blas_threads()
+
+
+def one_thread_sample():
+    """The same sample with one BLAS thread, in a child process (the thread count is fixed
+    when NumPy loads).  Returns RG steps/s or None."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import sys; sys.path.insert(0, %r); import bench; "
+            "print(bench.oracle_sample(min_seconds=1.0)[0])" % ROOT)
     try:
-        from threadpoolctl import threadpool_info
-        threads = max((d.get("num_threads", 0) for d in threadpool_info()), default=os.cpu_count())
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                           timeout=300)
+        return 1.0 / float(r.stdout.strip().splitlines()[-1])
     except Exception:
-        threads = os.cpu_count()
-    return per_step, desc, threads
+        return None
+
+
+def cpu_baseline_record(min_seconds):
+    per, desc, threads = oracle_sample(min_seconds=min_seconds)
+    return {"value": 1.0 / per, "unit": "RG steps/s", "cores": threads, "kind": "oracle",
+            "sample": desc, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "value_1_thread": one_thread_sample()}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(min_seconds=min(2.0, args.sample_seconds))
+        oracle_sample(min_seconds=0.0)
     times = []
     desc, threads = "", os.cpu_count()
     for _ in range(args.steps):
-        per_step, desc, threads = oracle_sample(
-            min_seconds=max(min(2.0, args.sample_seconds), args.sample_seconds / max(args.steps, 1)))
+        per_step, desc, threads = oracle_sample(min_seconds=args.sample_seconds / max(args.steps, 1))
         times.append(per_step)
     per = sum(times) / len(times)
     value = 1.0 / per
     line = {
-        "impl": "reference", "metric": "RG steps/s at chi=48 (split precision); TFLOP/s; df vs FP64 oracle",
+        "impl": "reference", "metric": METRIC,
         "value": value, "unit": "RG steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "chi": CHI, "r": R, "q": Q},
         "cpu_baseline": {"value": value, "unit": "RG steps/s", "cores": threads, "kind": "oracle",
-                         "sample": desc},
+                         "sample": desc + "; each timed step is one such sample, ms_per_step is "
+                         "the extrapolated step time", "cpu_model": cpu_model(),
+                         "nproc": os.cpu_count()},
         "e2e": {"value": value, "unit": "RG steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -286,10 +319,14 @@ def run_ours(args, world, rank, local):
     peaks, src = measured_peaks()
     bf16 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
     if prec == tg.TF32X3:
-        peak, note = bf16 * (1.1 / 2.25), "%s bf16 sustained x nominal tf32/bf16 (1.1/2.25)" % src
+        peak = bf16 * (1.1 / 2.25)
+        note = ("tf32 peak derived, not measured: %s bf16 sustained %.0f TFLOP/s x the nominal "
+                "dense tf32/bf16 ratio 1.1/2.25" % (src, bf16))
     else:
         peak, note = bf16, "%s bf16 sustained" % src
-    achieved = 3.0 * tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
+    # achieved: algorithmic flops (2 M N K per contraction) over the kernel's device time;
+    # the split form issues 3 tensor-core products per algorithmic one
+    achieved = tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
     traffic = None  # DRAM bytes per launch from the committed ncu capture of this workload
     prof = os.path.join(ROOT, "profiles", "tc_gemm_chi48_traffic.json")
     if os.path.exists(prof) and (chi, r) == (CHI, R) and prec == tg.TF32X3:
@@ -314,7 +351,7 @@ def run_ours(args, world, rank, local):
     workload = WORKLOAD if (chi, r) == (CHI, R) else WORKLOAD.replace(
         "chi=48 r=3", "chi=%d r=%d" % (chi, r)).replace("legs 48^4, bond 48", "legs %d^4, bond %d" % (chi, chi))
     line = {
-        "metric": "RG steps/s at chi=48 (split precision); TFLOP/s; df vs FP64 oracle",
+        "metric": METRIC,
         "value": value, "unit": "RG steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
@@ -322,13 +359,24 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs larger than L2 (each step streams > 10 GB of tensors)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "tflops_algorithmic": alg_flops / (ms / 1e3) / 1e12,
+        "tflops_algorithmic_note": "flops the library counts for the executed contractions; "
+                                   "tflops_cost_formula uses the steady-state cost formula",
+        "tflops_cost_formula": step_flops(chi, r, Q) / (ms / (1e3 * args.steps)) / 1e12,
         "stage_ms": dict(zip(["swap", "triad", "squeeze", "contract", "resplit"], stage_ms)),
         "roofline": {"bound": "tensor", "kernel": "tc_gemm_kernel (tcgen05 3-product split GEMM)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "peak_source": note, "launches": tc_launches,
+                     "frac": (achieved / peak) if achieved else None,
+                     "frac_algorithmic": (achieved / peak) if achieved else None,
+                     "traffic": traffic, "peak_source": note,
+                     "launches": tc_launches, "launches_note": "tensor-core launches on the "
+                     "context's stream; the small GEMMs of the factorisations that run concurrently "
+                     "on worker streams are not timed here",
                      "avg_launch_ms": tc_ms / max(tc_launches, 1),
-                     "flops_per_launch": 3.0 * tc_flops / max(tc_launches, 1)},
+                     "flops_per_launch": tc_flops / max(tc_launches, 1),
+                     "hardware_products": {
+                         "achieved": 3.0 * achieved if achieved else None,
+                         "frac": (3.0 * achieved / peak) if achieved else None,
+                         "note": "3 tensor-core products per algorithmic product (hi*hi, hi*lo, lo*hi)"}},
         "e2e": {"value": e2e_steps * world / e2e_s, "unit": "RG steps/s",
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "gpu_launches": launches,
@@ -338,9 +386,7 @@ def run_ours(args, world, rank, local):
         "delta_f": df,
     }
     if not args.no_cpu_baseline:
-        per, desc, threads = oracle_sample(min_seconds=10.0)
-        line["cpu_baseline"] = {"value": 1.0 / per, "unit": "RG steps/s", "cores": threads,
-                                "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = cpu_baseline_record(10.0)
     print(json.dumps(line), flush=True)
 
 

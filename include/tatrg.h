@@ -134,7 +134,9 @@ tatrg_status tatrg_get_state(const tatrg_ctx* ctx, int* d, int* dims, double* A,
                              double* B);
 
 /* Replace the state by host tensors (same layout as tatrg_get_state), with `step` steps
- * already taken and `partial_lnz` = sum_k 2^-k ln c_k so far.  Synchronises. */
+ * already taken and `partial_lnz` = sum_k 2^-k ln c_k so far.  Synchronises.  ENOMEM when
+ * the device buffers cannot be allocated; ENUMERIC when A, s or B holds a non-finite
+ * value.  On an error the previous state is kept. */
 tatrg_status tatrg_set_state(tatrg_ctx* ctx, int d, const int* dims, const double* A,
                              const double* s, const double* B, int step, double partial_lnz);
 
@@ -220,15 +222,35 @@ tatrg_status tatrg_svd(int64_t m, int64_t n, const double* A, double* U, double*
  * pool, a fixed reservation), or code where the implicit synchronisation of cudaMalloc /
  * cudaFree is not allowed.  The paper has no counterpart; this is a property of the
  * library.  No memory is allocated: the workspace is one fixed device array of 2 MiB
- * that every GPU loading the library keeps until the process exits, so the size limit is
- * (m + N + 3) * N + 3 <= 262144 doubles with N = n rounded up to even (e.g. n = 144 with
- * m <= 1670, n = 256 with m <= 762); larger inputs return TATRG_EINVAL.  The first call on
- * a device looks up that array's device address (make it before any stream capture).  All
+ * (262144 doubles) that every GPU loading the library keeps until the process exits, so
+ * the size limit is (m + N + 2) * N + 3 <= 262144 with N = n rounded up to even: for
+ * example n = 144 allows m <= 1674, n = 256 allows m <= 765, n = 2 allows m <= 131066.
+ * Larger inputs return TATRG_EINVAL.  The first call on a device looks up that array's
+ * device address; make that first call before any stream capture on the device.  All
  * calls share the array: calls whose work overlaps on the GPU race; each call rewrites
- * the whole workspace it reads.  Pointers are device pointers with the layout of
+ * every part of the workspace it reads.  Pointers are device pointers with the layout of
  * tatrg_svd; the call synchronises the stream.  Errors go to tatrg_last_error(NULL). */
 tatrg_status tatrg_svd_noalloc(int64_t m, int64_t n, const double* A, double* U, double* S,
                                double* V, void* cuda_stream);
+
+/* Raw words of the sketch generator (A10; the RSVD test matrices of Table 1): for counter
+ * blocks p = first .. first + npairs - 1, the four 32-bit outputs of Philox4x32-10 with
+ * counter (lo32(p), hi32(p), replica, hi32(seed)) and key (lo32(seed), stream_id), written
+ * to the device array `out` (4 * npairs words, word j of block p at 4 (p - first) + j;
+ * 16-byte aligned); p wraps modulo 2^64.  These are the integers every Gaussian sketch of
+ * tatrg_gaussian and of the operand packer is made from; they are exposed so the stream
+ * can be compared bit for bit.  EINVAL when npairs < 0 or out is null or unaligned. */
+tatrg_status tatrg_philox_words(unsigned long long seed, uint32_t stream_id, uint32_t replica,
+                                uint64_t first, int64_t npairs, uint32_t* out, void* cuda_stream);
+
+/* Time limit of the grid-wide barrier between the rounds of the cooperative Jacobi SVD
+ * (every core SVD of the step with n >= 32), in nanoseconds, for the current device; the
+ * default is 2e9 (2 s).  When a block waits longer, every block of that launch returns
+ * and the SVD reports TATRG_ETIMEOUT; the context stays usable.  The paper has no
+ * counterpart: this is the library's failure detection, and the setter exists so that
+ * a test can make the wait run out (a limit of 0 expires at the first wait).  It does not
+ * change the bounded waits of the tensor-core pipeline.  EINVAL for a negative limit. */
+tatrg_status tatrg_set_barrier_limit_ns(long long limit_ns);
 
 #ifdef __cplusplus
 }

@@ -340,26 +340,51 @@ def _group_core(U1, U2, Ws, g, cnt, left):
     return np.transpose(pm, (0, 3, 1, 2))
 
 
+QF_BLOCK_DOUBLES = 1 << 28  # largest block of the C2 intermediate held at once (2 GB)
+
+
+def _c2_c4(em, F, pf, g, cnt):
+    """C2 then C4 of one side (Eqs. 6-7), for blocks of consecutive gamma at a time.
+
+    C2: qf[i, k, z, l, gamma] = sum_{a, y} em[i, k, a, y, z] F[a, l, y, gamma];
+    C4: out[i, u.., z, gamma] = sum_{k, l} qf[i, k, z, l, gamma] pf[k, l, u..].
+    Each output column gamma is computed from the same terms whatever the block; the blocks
+    only bound the host memory of qf (18 GB at chi = 48, r = 3 if held whole)."""
+    st = "contract"
+    i, k, _, _, z = em.shape
+    l, Dg = F.shape[1], F.shape[3]
+    gb = max(1, min(Dg, QF_BLOCK_DOUBLES // (i * k * z * l)))
+    out = None
+    for g0 in range(0, Dg, gb):
+        qf = _c(cnt, st, "ikayz,alyg->ikzlg", em, F[:, :, :, g0:g0 + gb])   # C2
+        if g == 0:
+            blk = qf[:, 0, :, 0, :]
+        elif g == 1:
+            blk = _c(cnt, st, "ikzlg,klu->iuzg", qf, pf)                    # C4
+        else:
+            blk = _c(cnt, st, "ikzlg,kluv->iuvzg", qf, pf)                  # C4
+        if out is None:
+            out = np.empty(blk.shape[:-1] + (Dg,))
+        out[..., g0:g0 + gb] = blk
+        del qf
+    return out
+
+
 def contract(E, F, G, H, I, J, K, L, Ms, Ns, g, cnt=None):
-    """Eqs. 6-7.  Phi[i1, k_2..k_d, gamma] and Psi[j1, k'_2..k'_d, gamma]."""
+    """Eqs. 6-7.  Phi[i1, k_2..k_d, gamma] and Psi[j1, k'_2..k'_d, gamma].
+
+    Phi: C1 em = E M_sep, C2 with F, C3 pf from I, J and the group squeezers M_nu, C4.
+    Psi: the same chain with H (for E), G (for F), K, L and the N_nu."""
     st = "contract"
     Msep, Nsep = Ms[g], Ns[g]
-    em = _c(cnt, st, "ikxa,xyz->ikayz", E, Msep)            # C1
-    qf = _c(cnt, st, "ikayz,alyg->ikzlg", em, F)            # C2 [i, kA, k_sep, kX, gamma]
     pf = _group_core(I, J, Ms[:g], g, cnt, True)           # C3 [kA, kX, k_G]
-    hn = _c(cnt, st, "jkyd,zxy->jkdxz", H, Nsep)            # C1'
-    qp = _c(cnt, st, "jkdxz,dlxg->jkzlg", hn, G)            # C2' [j, kD, k_sep, kY, gamma]
     pp = _group_core(K, L, Ns[:g], g, cnt, False)          # C3' [kY, kD, k_G]
     pp = np.swapaxes(pp, 0, 1)                             #     [kD, kY, k_G]
-    if g == 0:
-        phi = qf[:, 0, :, 0, :]
-        psi = qp[:, 0, :, 0, :]
-    elif g == 1:
-        phi = _c(cnt, st, "ikzlg,klu->iuzg", qf, pf)        # C4
-        psi = _c(cnt, st, "jkzlg,klu->juzg", qp, pp)
-    else:
-        phi = _c(cnt, st, "ikzlg,kluv->iuvzg", qf, pf)      # C4
-        psi = _c(cnt, st, "jkzlg,kluv->juvzg", qp, pp)
+    em = _c(cnt, st, "ikxa,xyz->ikayz", E, Msep)            # C1  [i, kA, a, y, k_sep]
+    phi = _c2_c4(em, F, pf, g, cnt)
+    del em
+    hn = _c(cnt, st, "jkyd,zxy->jkdxz", H, Nsep)            # C1' [j, kD, d, x, k_sep]
+    psi = _c2_c4(hn, G, pp, g, cnt)
     return phi, psi
 
 

@@ -76,6 +76,8 @@ def lib():
             "tatrg_orth": [I, I64, I64, P, P, P, ctypes.POINTER(I), P],
             "tatrg_svd": [I64, I64, P, P, P, P, P],
             "tatrg_svd_noalloc": [I64, I64, P, P, P, P, P],
+            "tatrg_philox_words": [U64, U32, U32, U64, I64, P, P],
+            "tatrg_set_barrier_limit_ns": [ctypes.c_longlong],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -256,6 +258,20 @@ def svd_noalloc(A, U, S, V, stream=None):
     _check(lib().tatrg_svd_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(U.data_ptr()),
                                    ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
                                    _stream_ptr(stream)))
+
+
+def philox_words(seed, stream_id, first, npairs, out, replica=0, stream=None):
+    """Raw Philox4x32-10 words of counter blocks first .. first + npairs - 1 into the int32
+    CUDA tensor `out` (4 words per block)."""
+    assert out.is_cuda and out.numel() >= 4 * npairs
+    _check(lib().tatrg_philox_words(seed, stream_id, replica, first, npairs,
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def set_barrier_limit_ns(limit_ns):
+    """Time limit of the cooperative Jacobi SVD's grid-barrier waits on the current device."""
+    _check(lib().tatrg_set_barrier_limit_ns(int(limit_ns)))
 
 
 def lnz_function(chi, r, q=2, method=TRIAD, precision=FP64, seed=0, d=4, nsteps=8):

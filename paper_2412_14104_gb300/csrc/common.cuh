@@ -92,6 +92,7 @@ class DevBuf {
       cudaError_t e = cudaMallocAsync(&p_, bytes, s);
       if (e != cudaSuccess) {
         p_ = nullptr;
+        cudaGetLastError();  // an allocation failure is not sticky: clear it for later checks
         throw Error(TATRG_ENOMEM, "cudaMallocAsync(" + std::to_string(bytes) + "): " +
                                       cudaGetErrorString(e));
       }

@@ -41,6 +41,13 @@ struct Stats {
 };
 
 // kernels_f64.cu ----------------------------------------------------------------------
+// multiprocessors of the current device (cached per device ordinal)
+int sm_count();
+// raise a kernel's dynamic shared-memory limit to `bytes` on the current device (once)
+void ensure_smem_attr(const void* fn, int bytes);
+// raw Philox4x32-10 words of counter blocks first .. first + npairs - 1 (philox.cuh)
+void philox_words(uint64_t seed, uint32_t sid, uint32_t replica, uint64_t first, int64_t npairs,
+                  uint32_t* out, cudaStream_t s);
 void gemm_f64(const GemmDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
               Stats* st);
 // Philox4x32-10 Gaussians; float_math evaluates Box-Muller in float (split-precision
@@ -81,6 +88,9 @@ void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStre
 // synchronises the stream.
 void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S, double* V,
                         cudaStream_t s);
+
+// time limit of the cooperative Jacobi's grid-barrier waits on the current device
+void set_barrier_limit_ns(unsigned long long ns);
 
 // tc_gemm.cu --------------------------------------------------------------------------
 // Split-precision tcgen05 GEMM on multi-mode operands: prec 1 = 3xTF32, 2 = BF16x3.

@@ -221,7 +221,7 @@ void gemm_f64(const GemmDesc& d0, const double* A, const double* B, double* C, c
   g.b_ncontig = stride1_first(d.n, true) && !stride1_first(d.k, false);
   const int64_t tiles = cdiv(M, BM) * cdiv(N, BN);
   int split = 1;
-  const int64_t target = 4 * 152;
+  const int64_t target = 4 * int64_t(sm_count());
   if (tiles < target && K > 4 * BK) {
     split = int(std::min<int64_t>(cdiv(target, tiles), cdiv(K, 4 * BK)));
     split = std::min(split, 1024);
@@ -298,13 +298,66 @@ __global__ void gaussian_f32_kernel(uint64_t seed, uint32_t sid, uint32_t replic
 }
 }  // namespace
 
+namespace {
+__global__ void philox_words_kernel(uint64_t seed, uint32_t sid, uint32_t replica, uint64_t first,
+                                    int64_t npairs, uint4* out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < npairs;
+       i += int64_t(gridDim.x) * blockDim.x) {
+    uint32_t w[4];
+    philox4x32_10(seed, sid, replica, int64_t(first + uint64_t(i)), w);  // counter modulo 2^64
+    out[i] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+}  // namespace
+
+void philox_words(uint64_t seed, uint32_t sid, uint32_t replica, uint64_t first, int64_t npairs,
+                  uint32_t* out, cudaStream_t s) {
+  TATRG_CHECK(out != nullptr && npairs >= 0, TATRG_EINVAL, "philox_words: bad argument");
+  TATRG_CHECK((reinterpret_cast<uintptr_t>(out) & 15) == 0, TATRG_EINVAL,
+              "philox_words: output must be 16-byte aligned");
+  if (npairs == 0) return;
+  check_extent(out, 4 * npairs - 1, sizeof(uint32_t), "philox_words");
+  const int blocks = int(std::min<int64_t>(cdiv(npairs, 256), int64_t(sm_count()) * 32));
+  philox_words_kernel<<<blocks, 256, 0, s>>>(seed, sid, replica, first, npairs, reinterpret_cast<uint4*>(out));
+  TATRG_CUDA(cudaGetLastError());
+}
+
+void ensure_smem_attr(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> done;
+  int dev = 0;
+  TATRG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> l(mu);
+  auto key = std::make_pair(dev, fn);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return;
+  TATRG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done[key] = bytes;
+}
+
+int sm_count() {
+  // per device ordinal: a process may drive several GPUs
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  TATRG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> l(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  TATRG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  TATRG_CHECK(n >= 1, TATRG_ECUDA, "device reports no multiprocessors");
+  cache[dev] = n;
+  return n;
+}
+
 void gaussian(uint64_t seed, uint32_t sid, uint32_t replica, int64_t n, double* out,
               cudaStream_t s, bool float_math) {
   if (n <= 0) return;
   TATRG_CHECK(out != nullptr, TATRG_EINVAL, "gaussian: null output");
   check_extent(out, n - 1, sizeof(double), "gaussian");
   int64_t npairs = (n + 1) / 2;
-  int blocks = int(std::min<int64_t>(cdiv(npairs, 256), 152 * 32));
+  int blocks = int(std::min<int64_t>(cdiv(npairs, 256), int64_t(sm_count()) * 32));
   if (float_math) {
     TATRG_CHECK((reinterpret_cast<uintptr_t>(out) & 15) == 0, TATRG_EINVAL,
                 "gaussian: output must be 16-byte aligned");
@@ -483,7 +536,7 @@ __global__ void check_finite_kernel(const double* x, int64_t n, int* bad) {
     if (!isfinite(x[e])) { *bad = 1; return; }
 }
 
-int grid_for(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 16))); }
+int grid_for(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), int64_t(sm_count()) * 16))); }
 }  // namespace
 
 void scale_axis(double* x, const double* v, int64_t outer, int64_t n, int64_t inner, int power,
@@ -507,7 +560,7 @@ void copy_modes(double* dst, const double* src, const ModeIdx& m, double alpha, 
 
 namespace {
 // rows per block for the row-chunked reductions: about 4 blocks per SM
-int64_t row_chunk(int64_t F) { return std::max<int64_t>(64, cdiv(F, 4 * 152)); }
+int64_t row_chunk(int64_t F) { return std::max<int64_t>(64, cdiv(F, 4 * int64_t(sm_count()))); }
 
 void finish_partials(const double* part, int nb, int width, double* out, cudaStream_t s) {
   finish_partials_kernel<<<int(cdiv(width, 256)), 256, 0, s>>>(part, nb, width, out);

@@ -329,11 +329,15 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Time limit of one grid-barrier wait (2 s unless a caller changed it on this device).
+__device__ unsigned long long g_barrier_limit_ns = 2000000000ull;
+
 // Grid-wide barrier over co-resident blocks with a time limit.  bar[0] counts arrivals,
 // bar[1] is the generation, bar[2] the abort flag.  Thread 0 of each block reads the
 // generation, arrives, and the last block to arrive resets the count and advances the
-// generation; the others wait for that, at most 2 s, after which they set the abort flag.
-// Every block returns false once the abort flag is set, so no block waits for ever.
+// generation; the others wait for that, at most g_barrier_limit_ns, after which they set
+// the abort flag.  Every block returns false once the abort flag is set, so no block
+// waits for ever.
 __device__ bool grid_barrier(unsigned* bar) {
   __shared__ int ok;
   __syncthreads();
@@ -347,9 +351,9 @@ __device__ bool grid_barrier(unsigned* bar) {
       atomicAdd(&bar[1], 1u);
       ok = 1;
     } else {
-      const uint64_t t0 = global_ns();
+      const uint64_t t0 = global_ns(), limit = g_barrier_limit_ns;
       while (vb[1] == gen && vb[2] == 0u) {
-        if (global_ns() - t0 > 2000000000ull) { atomicExch(&bar[2], 1u); break; }
+        if (global_ns() - t0 >= limit) { atomicExch(&bar[2], 1u); break; }
         __nanosleep(64);
       }
       ok = vb[1] != gen;
@@ -502,6 +506,11 @@ __global__ void sumsq_kernel(const double* x, int64_t n, double* out) {
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
+// The single-block Jacobi keeps the whole m x N column-major copy in shared memory
+// (at most 200 KB); it is used for narrow matrices (N < 32) that fit.  Everything else,
+// including N = 2 with a tall m, takes the multi-block kernels, which handle one column
+// pair as well.
+bool single_block_fits(int64_t m, int N) { return N < 32 && m * N * int64_t(sizeof(double)) <= 200 * 1024; }
 }  // namespace
 
 void cholesky(const double* G, int n, double* R, int* status_dev, double shift_rel,
@@ -510,9 +519,7 @@ void cholesky(const double* G, int n, double* R, int* status_dev, double shift_r
   check_extent(R, int64_t(n) * n - 1, sizeof(double), "cholesky output");
   TATRG_CHECK(n >= 1 && n <= 160, TATRG_EINVAL, "cholesky: n must be <= 160");
   const size_t sm = size_t(n) * n * sizeof(double);
-  static const cudaError_t attr = cudaFuncSetAttribute(  // once, thread-safe
-      cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 160 * 8);
-  TATRG_CUDA(attr);
+  ensure_smem_attr(reinterpret_cast<const void*>(cholesky_kernel), 160 * 160 * 8);
   cholesky_kernel<<<1, 1024, sm, s>>>(G, n, R, status_dev, shift_rel);
   TATRG_CUDA(cudaGetLastError());
 }
@@ -522,9 +529,7 @@ void tri_inverse(const double* R, int n, double* Rinv, cudaStream_t s) {
   check_extent(Rinv, int64_t(n) * n - 1, sizeof(double), "tri_inverse output");
   TATRG_CHECK(n >= 1 && n <= 1024, TATRG_EINVAL, "tri_inverse: n must be <= 1024");
   if (n <= 160) {
-    static const cudaError_t attr = cudaFuncSetAttribute(  // once, thread-safe
-        tri_inverse_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (160 * 160 + 4 * 160) * 8);
-    TATRG_CUDA(attr);
+    ensure_smem_attr(reinterpret_cast<const void*>(tri_inverse_kernel<true>), (160 * 160 + 4 * 160) * 8);
     tri_inverse_kernel<true><<<(n + 3) / 4, 128, size_t(n * n + 4 * n) * sizeof(double), s>>>(R, n, Rinv);
   } else {
     tri_inverse_kernel<false><<<(n + 3) / 4, 128, 4 * n * sizeof(double), s>>>(R, n, Rinv);
@@ -546,11 +551,9 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
                                                                                   ac.d(), vc.d());
   TATRG_CUDA(cudaGetLastError());
   const double tol = std::max(1e-15, 2.220446049250313e-16 * std::sqrt(double(m)));
-  if ((m * N * 8 <= 200 * 1024 && N < 32) || N < 4) {
+  if (single_block_fits(m, N)) {
     int threads = 32 * std::max(1, std::min(32, N / 2));
-    static const cudaError_t attr = cudaFuncSetAttribute(  // once, thread-safe
-        jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    TATRG_CUDA(attr);
+    ensure_smem_attr(reinterpret_cast<const void*>(jacobi_kernel), 200 * 1024);
     jacobi_kernel<<<1, threads, size_t(m * N) * sizeof(double), s>>>(ac.d(), m, N, vc.d(), 60, tol, status_dev);
     TATRG_CUDA(cudaGetLastError());
   } else {
@@ -584,7 +587,7 @@ void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double*
   col_norms_kernel<<<n, 256, 0, s>>>(ac.d(), m, sig.d());
   rank_kernel<<<1, 1024, 0, s>>>(sig.d(), n, rk.as<int>(), S);
   int64_t tot2 = m * n + int64_t(n) * n;
-  svd_scatter_kernel<<<int(std::min<int64_t>(cdiv(tot2, 256), 152 * 16)), 256, 0, s>>>(
+  svd_scatter_kernel<<<int(std::min<int64_t>(cdiv(tot2, 256), int64_t(sm_count()) * 16)), 256, 0, s>>>(
       ac.d(), m, n, N, vc.d(), sig.d(), rk.as<int>(), U, V);
   TATRG_CUDA(cudaGetLastError());
   if (st) st->launches += 5;
@@ -634,8 +637,8 @@ void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S,
   TATRG_CHECK(m >= n && n >= 1 && n <= 1024, TATRG_EINVAL, "svd_noalloc: need m >= n, 1 <= n <= 1024");
   const int64_t need = svd_noalloc_scratch_needed(m, n);
   TATRG_CHECK(need <= kSvdScratchDoubles, TATRG_EINVAL,
-              "svd_noalloc: m x n too large for the fixed scratch (needs (m + n + 3) * n + 3 "
-              "<= 262144 doubles for even n)");
+              "svd_noalloc: m x n too large for the fixed scratch: needs (m + N + 2) * N + 3 <= "
+              "262144 doubles, N = n rounded up to even");
   double* base = svd_scratch_address();
   const int N = n + (n & 1);
   double* ac = base;
@@ -650,7 +653,7 @@ void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S,
   TATRG_CUDA(cudaGetLastError());
   const double tol = std::max(1e-15, 2.220446049250313e-16 * std::sqrt(double(m)));
   int converged = 0;
-  if ((m * N * 8 <= 200 * 1024 && N < 32) || N < 4) {
+  if (single_block_fits(m, N)) {
     int threads = 32 * std::max(1, std::min(32, N / 2));
     TATRG_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     jacobi_kernel<<<1, threads, size_t(m * N) * sizeof(double), s>>>(ac, m, N, vc, 60, tol, status);
@@ -680,10 +683,14 @@ void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S,
   col_norms_kernel<<<n, 256, 0, s>>>(ac, m, sig);
   rank_kernel<<<1, 1024, 0, s>>>(sig, n, rk, S);
   int64_t tot2 = m * n + int64_t(n) * n;
-  svd_scatter_kernel<<<int(std::min<int64_t>(cdiv(tot2, 256), 152 * 16)), 256, 0, s>>>(ac, m, n, N, vc,
+  svd_scatter_kernel<<<int(std::min<int64_t>(cdiv(tot2, 256), int64_t(sm_count()) * 16)), 256, 0, s>>>(ac, m, n, N, vc,
                                                                                        sig, rk, U, V);
   TATRG_CUDA(cudaGetLastError());
   TATRG_CUDA(cudaStreamSynchronize(s));
+}
+
+void set_barrier_limit_ns(unsigned long long ns) {
+  TATRG_CUDA(cudaMemcpyToSymbol(g_barrier_limit_ns, &ns, sizeof(ns)));
 }
 
 void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStream_t s) {

@@ -106,7 +106,7 @@ __global__ void ising_tensor_tan_kernel(double beta, double h, int d, int dir, d
   }
 }
 
-int blocks_for(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), 152 * 16))); }
+int blocks_for(int64_t n) { return int(std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 256), int64_t(sm_count()) * 16))); }
 }  // namespace
 
 std::vector<int> multiplet_groups(const std::vector<double>& v, double tau) {

@@ -1553,14 +1553,27 @@ tatrg_status tatrg_set_state(tatrg_ctx* ctx, int d, const int* dims, const doubl
   return guard(ctx, [&] {
     TATRG_CHECK(d >= 2 && d <= 4 && step >= 0, TATRG_EINVAL, "tatrg_set_state: bad d or step");
     for (int i = 0; i <= d; ++i) TATRG_CHECK(dims[i] >= 1, TATRG_EINVAL, "tatrg_set_state: bad dims");
+    for (int i = 0; i < dims[d]; ++i)
+      TATRG_CHECK(std::isfinite(s[i]), TATRG_ENUMERIC, "tatrg_set_state: non-finite entry in s");
+    std::vector<int64_t> D(dims, dims + d);
+    const int64_t F = prod(D, 0, D.size()), Da = dims[d];
+    // upload and check into new buffers; the context's state changes only when both pass
+    DevBuf nA(F * Da * sizeof(double), ctx->stream), nB(F * Da * sizeof(double), ctx->stream);
+    TATRG_CUDA(cudaMemcpyAsync(nA.d(), A, F * Da * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    TATRG_CUDA(cudaMemcpyAsync(nB.d(), B, F * Da * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    DevBuf bad(sizeof(int), ctx->stream);
+    TATRG_CUDA(cudaMemsetAsync(bad.d(), 0, sizeof(int), ctx->stream));
+    check_finite(nA.d(), F * Da, bad.as<int>(), ctx->stream);
+    check_finite(nB.d(), F * Da, bad.as<int>(), ctx->stream);
+    int hbad = 0;
+    TATRG_CUDA(cudaMemcpyAsync(&hbad, bad.d(), sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    TATRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    TATRG_CHECK(hbad == 0, TATRG_ENUMERIC, "tatrg_set_state: non-finite entries in A or B");
     ctx->d = d;
-    ctx->D.assign(dims, dims + d);
-    ctx->Da = dims[d];
-    const int64_t F = prod(ctx->D, 0, ctx->D.size());
-    ctx->A = DevBuf(F * ctx->Da * sizeof(double), ctx->stream);
-    ctx->B = DevBuf(F * ctx->Da * sizeof(double), ctx->stream);
-    TATRG_CUDA(cudaMemcpyAsync(ctx->A.d(), A, F * ctx->Da * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    TATRG_CUDA(cudaMemcpyAsync(ctx->B.d(), B, F * ctx->Da * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    ctx->D = D;
+    ctx->Da = Da;
+    ctx->A = std::move(nA);
+    ctx->B = std::move(nB);
     ctx->s.assign(s, s + ctx->Da);
     ctx->upload_s();
     ctx->step = step;
@@ -1697,6 +1710,21 @@ tatrg_status tatrg_svd_noalloc(int64_t m, int64_t n, const double* A, double* U,
     TATRG_CHECK(A && U && S && V, TATRG_EINVAL, "tatrg_svd_noalloc: null argument");
     TATRG_CHECK(n >= 1 && n <= 1024 && m >= n, TATRG_EINVAL, "tatrg_svd_noalloc: need m >= n, 1 <= n <= 1024");
     jacobi_svd_noalloc(A, m, int(n), U, S, V, static_cast<cudaStream_t>(stream));
+  });
+}
+
+tatrg_status tatrg_philox_words(unsigned long long seed, uint32_t sid, uint32_t replica, uint64_t first,
+                                int64_t npairs, uint32_t* out, void* stream) {
+  return guard(nullptr, [&] {
+    TATRG_CHECK(out && npairs >= 0, TATRG_EINVAL, "tatrg_philox_words: bad argument");
+    philox_words(seed, sid, replica, first, npairs, out, static_cast<cudaStream_t>(stream));
+  });
+}
+
+tatrg_status tatrg_set_barrier_limit_ns(long long limit_ns) {
+  return guard(nullptr, [&] {
+    TATRG_CHECK(limit_ns >= 0, TATRG_EINVAL, "tatrg_set_barrier_limit_ns: negative limit");
+    set_barrier_limit_ns(static_cast<unsigned long long>(limit_ns));
   });
 }
 

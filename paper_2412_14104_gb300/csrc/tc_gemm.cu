@@ -714,15 +714,21 @@ void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& b
   static_assert(KC >= 1, "an FP32 chain spans at least one stage");
   constexpr int SMEM = STAGES * STAGE + 1024;
   auto k = tc_gemm_kernel<PREC, KC, STAGES, 2>;
-  static const cudaError_t attr =  // once per instantiation, thread-safe
-      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-  TATRG_CUDA(attr);
-  static const int resident = [&]() {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, TC_THREADS, SMEM) != cudaSuccess) n = 0;
-    return n;
-  }();
-  TATRG_CHECK(resident >= 1, TATRG_ECUDA, "gemm_tc: the tensor-core kernel does not fit on an SM");
+  // the shared-memory attribute and the occupancy check, once per device and instantiation
+  static std::mutex mu;
+  static std::map<int, int> resident_on;
+  int dev = 0;
+  TATRG_CUDA(cudaGetDevice(&dev));
+  {
+    std::lock_guard<std::mutex> l(mu);
+    if (!resident_on.count(dev)) {
+      TATRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+      int n = 0;
+      TATRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, TC_THREADS, SMEM));
+      resident_on[dev] = n;
+    }
+    TATRG_CHECK(resident_on[dev] >= 1, TATRG_ECUDA, "gemm_tc: the tensor-core kernel does not fit on an SM");
+  }
   k<<<grid, TC_THREADS, SMEM, s>>>(ahi, alo, bhi, blo, a);
   TATRG_CUDA(cudaGetLastError());
 }
@@ -730,13 +736,19 @@ void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& b
 }  // namespace
 
 bool tc_available() {
-  static const bool ok = []() {  // once, thread-safe
-    int dev = 0, major = 0, minor = 0;
-    return cudaGetDevice(&dev) == cudaSuccess &&
-           cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
-           cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess &&
-           major == 10 && minor == 3 && encode_fn() != nullptr;
-  }();
+  // per device ordinal: a process may drive several GPUs
+  static std::mutex mu;
+  static std::map<int, bool> ok_on;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> l(mu);
+  auto it = ok_on.find(dev);
+  if (it != ok_on.end()) return it->second;
+  int major = 0, minor = 0;
+  const bool ok = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) == cudaSuccess &&
+                  major == 10 && minor == 3 && encode_fn() != nullptr;
+  ok_on[dev] = ok;
   return ok;
 }
 
@@ -780,7 +792,7 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     DevModes rm = dev(d.m), km = dev(d.k);
     const int rc = (d.m.n > 0 && d.m.s0[d.m.n - 1] == 1 && !(d.k.n > 0 && d.k.s0[d.k.n - 1] == 1)) ? 1 : 0;
     const int64_t kt = cdiv(Kp, PK_K), ta = (Mp / PK_R) * kt;
-    const int ga = int(std::min<int64_t>(ta, 152 * 6));
+    const int ga = int(std::min<int64_t>(ta, int64_t(sm_count()) * 6));
     if (prec == 1) pack_kernel<1, false><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc, no_gen);
     else pack_kernel<2, false><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc, no_gen);
     TATRG_CUDA(cudaGetLastError());
@@ -796,7 +808,7 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     for (int i = 0; i < kMaxModes; ++i) kn.s0[i] = kn.s1[i];  // B's k strides
     const int rcb = (d.n.n > 0 && d.n.s0[d.n.n - 1] == 1 && !(d.k.n > 0 && d.k.s1[d.k.n - 1] == 1)) ? 1 : 0;
     const int64_t tb = (Np / PK_R) * kt;
-    const int gb = int(std::min<int64_t>(tb, 152 * 6));
+    const int gb = int(std::min<int64_t>(tb, int64_t(sm_count()) * 6));
     if (!same) {
       if (gen_b) {
         if (prec == 1) pack_kernel<1, true><<<gb, 256, 0, s>>>(nullptr, rn, kn, N, K, Kp, kt, tb, bhi, blo, 0, *gen_b);
@@ -815,7 +827,8 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   const int nkb = int(Kp / kelem);
   const int64_t tiles = (Mp / TC_BM) * (Np / BN);
   int split = 1;
-  if (tiles < 2 * 152 && nkb >= 8) split = int(std::min<int64_t>(cdiv(2 * 152, tiles), nkb / 4));
+  const int64_t sms = sm_count();
+  if (tiles < 2 * sms && nkb >= 8) split = int(std::min<int64_t>(cdiv(2 * sms, tiles), nkb / 4));
   split = std::max(1, std::min(split, 512));
   const int per = int(cdiv(nkb, split));
   split = int(cdiv(nkb, per));
@@ -846,13 +859,6 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   const int64_t units = int64_t(a.mtiles) * a.ntiles * split;
   TATRG_CHECK(units < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: too many work units");
   // persistent: one CTA per SM (the shared-memory ring admits no second one)
-  static const int sms = []() {
-    int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
-      n = 1;
-    return n;
-  }();
   dim3 grid(unsigned(std::min<int64_t>(units, sms)));
   const bool timed = st && st->timing;
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));

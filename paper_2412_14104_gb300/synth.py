@@ -24,3 +24,12 @@ def split_state(seed, legs, Da, decay=0.9):
 
 def gaussian_matrix(seed, rows, cols):
     return np.random.default_rng(seed).standard_normal((rows, cols))
+
+
+def device_normal(seed, shape, device="cuda"):
+    """Seeded N(0, 1) float64 tensor generated on the device (torch's Philox generator):
+    full-size contraction operands that would take minutes to draw on the host."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    return torch.randn(shape, dtype=torch.float64, device=device, generator=gen)

@@ -68,3 +68,7 @@ def test_building_blocks_reject_bad_sizes_before_touching_memory(libpath):
     assert L.tatrg_orth(9, 8, 4, fake, fake, fake, ctypes.byref(k), None) == 1
     # sketches: negative sizes
     assert L.tatrg_gaussian(1, 2, 0, -1, 4, fake, None) == 1
+    # raw Philox words: negative count, null output; the wait limit: negative
+    assert L.tatrg_philox_words(1, 2, 0, 0, -1, fake, None) == 1
+    assert L.tatrg_philox_words(1, 2, 0, 0, 4, None, None) == 1
+    assert L.tatrg_set_barrier_limit_ns(-1) == 1

@@ -33,6 +33,32 @@ def test_philox_sketch_matches_oracle(torch, rows, cols, replica):
     assert np.allclose(got, want, rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("seed,sid,replica,first,npairs", [
+    (0, 0, 0, 0, 1), (2 ** 40 + 17, 0x503, 3, 0, 4099), (7, 0xFFFFFFFF, 2 ** 31 + 5, 2 ** 32 - 7, 300),
+    (2 ** 64 - 1, 1, 0, 2 ** 63 + 12345, 1000)])
+def test_philox_words_bit_identical_to_oracle(torch, seed, sid, replica, first, npairs):
+    """P12 on the raw integers: every output word of the device generator equals the
+    oracle's, including counters that cross the 32-bit word boundary and the top half of
+    the 64-bit counter range."""
+    out = torch.empty(4 * npairs, dtype=torch.int32, device="cuda")
+    tg.philox_words(seed, sid, first, npairs, out, replica=replica)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().view(np.uint32).reshape(npairs, 4)
+    want = np.stack(philox.philox_words(seed, sid, first, npairs, replica), axis=1)
+    assert np.array_equal(got, want)
+
+
+def test_philox_words_known_answers_on_gpu(torch):
+    """The published Philox4x32-10 known-answer vectors through the device stream mapping
+    (counter (lo p, hi p, replica, hi seed), key (lo seed, stream id))."""
+    from tests.test_oracle_pins import philox_kat
+    out = torch.empty(4, dtype=torch.int32, device="cuda")
+    for (c0, c1, c2, c3), (k0, k1), want in philox_kat():
+        tg.philox_words((c3 << 32) | k0, k1, (c1 << 32) | c0, 1, out, replica=c2)
+        torch.cuda.synchronize()
+        assert out.cpu().numpy().view(np.uint32).tolist() == want
+
+
 def _contract_case(rng, torch, prec, tol):
     # C[i,j,a,b] (stored [a,i,b,j]) = sum_{k,l} A[k,i,l,a] B[b,l,j,k]
     I, J, a, b, K, L = 5, 7, 3, 4, 6, 9

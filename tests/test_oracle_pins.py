@@ -1,6 +1,7 @@
 """Pins of the FP64 oracle against results fixed outside it (brute force, Onsager's closed
 form, the high-temperature series, exact linear algebra and symmetry).  CPU only."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -277,6 +278,38 @@ def test_philox_stream_layout():
     u2 = philox._uniform53(w2, w3)[0]
     assert a[10] == math.sqrt(-2 * math.log(u1)) * math.cos(2 * math.pi * u2)
     assert a[11] == math.sqrt(-2 * math.log(u1)) * math.sin(2 * math.pi * u2)
+
+
+def philox_kat():
+    """Rows of tests/golden/philox4x32_10_kat.txt: (counter[4], key[2], words[4])."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(x, 16) for x in line.split()]
+        rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    """P12's reference: the published Philox4x32-10 known answers (Random123).  A wrong
+    multiplier, Weyl increment, round count or word order fails this."""
+    rows = philox_kat()
+    assert len(rows) == 3
+    for (c0, c1, c2, c3), (k0, k1), want in rows:
+        got = philox.philox4x32_10([c0], [c1], [c2], [c3], k0, k1)
+        assert [int(w[0]) for w in got] == want
+
+
+def test_philox_words_follow_the_stream_layout():
+    """philox_words(seed, sid, p, ...) is Philox on counter (lo p, hi p, replica, hi seed) and
+    key (lo seed, sid): the KAT rows through the sketch-stream mapping."""
+    for (c0, c1, c2, c3), (k0, k1), want in philox_kat():
+        seed = (c3 << 32) | k0
+        p = (c1 << 32) | c0
+        w = philox.philox_words(seed, k1, p, 1, replica=c2)
+        assert [int(x[0]) for x in w] == want
 
 
 def test_philox_is_a_bijection_on_small_counters():
