@@ -252,6 +252,101 @@ def delta_f_check(tg):
     return out
 
 
+C3_STEPS = 40
+C3_FILE = os.path.join(ROOT, "profiles", "c3_chi48_runs.json")
+
+
+def parse_form(text):
+    """'fp64', 'tf32x3@13' (split precision from step 13), 'bf16x3' (from step 1)."""
+    name, _, start = text.partition("@")
+    return name, int(start) if start else 1
+
+
+def run_c3(args):
+    """The chi = 48, r = 3, q = 2, h = 1e-4, 40-step configuration in whole runs, one per form
+    in --c3-forms.  The FP64 run goes first; a form 'prec@k' (split precision from step k)
+    continues from the FP64 run's state after step k - 1 (its first k - 1 steps are FP64
+    steps, whose results repeat bit for bit), and its whole-run time is the FP64 run's time
+    for those steps plus its own.  Each run's ln c_k per step and ln Z / V are written to
+    profiles/c3_chi48_runs.json.  Prints one summary JSON line."""
+    import torch
+    import paper_2412_14104_gb300 as tg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    prec_of = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "fp64": tg.FP64}
+    forms = [parse_form(f) for f in args.c3_forms.split(",")]
+    branch_at = sorted({k for name, k in forms if name != "fp64" and k > 1})
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def run(name, start, state=None):
+        ctx = tg.Context(CHI, R, Q, seed=SEED, precision=prec_of[name], split_from_step=start,
+                         stream=stream)
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        if state is None:
+            ctx.init_ising(BETA, H, 4)
+            k0 = 0
+        else:
+            A, s, B, k0, part = state
+            ctx.set_state(A, s, B, k0, part)
+        lnc, step_s, saved = [], [], {}
+        for k in range(k0 + 1, C3_STEPS + 1):
+            if state is None and k in branch_at:
+                torch.cuda.synchronize()
+                A, s, B = ctx.get_state()
+                saved[k] = (A, s, B, k - 1, ctx.step_info().partial_lnz if k > 1 else None)
+            s0, s1 = ev(), ev()
+            s0.record(stream)
+            ctx.rg_step()
+            s1.record(stream)
+            torch.cuda.synchronize()
+            lnc.append(ctx.step_info().lnc)
+            step_s.append(s0.elapsed_time(s1) / 1e3)
+        lnz = ctx.lnZ()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ctx.close()
+        return {"lnz": lnz, "lnc": lnc, "step_s": step_s}, saved
+
+    out = {}
+    fp, saved = run("fp64", 1)
+    fp["run_s"] = sum(fp["step_s"])
+    out["fp64"] = dict(fp, precision="fp64", split_from_step=None)
+    print("fp64: lnZ/V = %.16f, %.1f s of steps" % (fp["lnz"], fp["run_s"]), flush=True)
+    for name, k in forms:
+        if name == "fp64":
+            continue
+        tag = "%s@%d" % (name, k)
+        res, _ = run(name, k, saved[k] if k > 1 else None)
+        res["lnc"] = fp["lnc"][:k - 1] + res["lnc"]
+        res["step_s"] = fp["step_s"][:k - 1] + res["step_s"]
+        res["run_s"] = sum(res["step_s"])
+        res["rel_to_fp64"] = abs(res["lnz"] - fp["lnz"]) / abs(fp["lnz"])
+        out[tag] = dict(res, precision=name, split_from_step=k)
+        print("%s: lnZ/V = %.16f, rel %.3e, %.1f s of steps" % (tag, res["lnz"], res["rel_to_fp64"],
+                                                                 res["run_s"]), flush=True)
+    out["fp64"]["rel_to_fp64"] = 0.0
+    doc = {"config": "chi=48 r=3 q=2 beta=0.1497 h=1e-4 seed 2, 40 steps, d=4",
+           "command": "python bench.py --c3-run --c3-forms " + args.c3_forms,
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+           "timing": "sum of per-step CUDA-event times (init and state copies excluded)",
+           "runs": out}
+    os.makedirs(os.path.dirname(C3_FILE), exist_ok=True)
+    with open(C3_FILE, "w") as f:
+        json.dump(doc, f, indent=1)
+    print(json.dumps(c3_summary(doc)), flush=True)
+
+
+def c3_summary(out):
+    """ln Z / V differences and whole-run times of the stored 40-step chi = 48 runs."""
+    runs = out["runs"]
+    return {"config": out["config"], "measured": out["when"], "command": out["command"],
+            "lnz_fp64_gpu": runs["fp64"]["lnz"] if "fp64" in runs else None,
+            "forms": {k: {"rel_to_fp64_gpu": v.get("rel_to_fp64"), "run_s": v["run_s"]}
+                      for k, v in runs.items()}}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -385,6 +480,12 @@ def run_ours(args, world, rank, local):
         "split_vs_fp64_speedup": (fp64_ms / (ms_max / args.steps)) if fp64_ms else None,
         "delta_f": df,
     }
+    if os.path.exists(C3_FILE) and (chi, r) == (CHI, R):
+        with open(C3_FILE) as f:
+            line["delta_f_chi48"] = dict(c3_summary(json.load(f)),
+                                         note="stored whole-run measurement (not re-run by this "
+                                              "command); the FP64 GPU step is checked against the "
+                                              "oracle by the chi = 48 teacher-forced step test")
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_record(10.0)
     print(json.dumps(line), flush=True)
@@ -405,7 +506,13 @@ def main():
     ap.add_argument("--r", type=int, default=R)
     ap.add_argument("--sample-seconds", type=float, default=20.0,
                     help="host seconds of oracle work the reference arm times (over all steps)")
+    ap.add_argument("--c3-run", action="store_true",
+                    help="run the 40-step chi = 48 configuration in the forms of --c3-forms")
+    ap.add_argument("--c3-forms", default="fp64,tf32x3@1,bf16x3@1,tf32x3@5,bf16x3@5,tf32x3@9,bf16x3@9,tf32x3@13,bf16x3@13")
     args = ap.parse_args()
+    if args.c3_run:
+        run_c3(args)
+        return
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

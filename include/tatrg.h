@@ -123,6 +123,22 @@ tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh,
 tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double h, int d,
                          int nsteps, double* lnZ_out);
 
+/* The same temperature runs, also writing to the host array X_out (nullable) the order
+ * parameter X^(m) of tatrg_order_parameter at leg position d - 1 after the last step of each
+ * run: the temperature scan of Sec. 3 that locates the transition point. */
+tatrg_status tatrg_sweep_observables(tatrg_ctx* ctx, const double* betas, int nbeta, double h,
+                                     int d, int nsteps, double* lnZ_out, double* X_out);
+
+/* Order parameter of the transition point (Sec. 3, the definition of X^(m) after Gu & Wen):
+ * A^(m)[k, l] = sum over every other leg x of T[.., x, k, ..; .., x, l, ..] with the forward
+ * leg at position `leg` open as k and its backward leg as l, and
+ * X = (Tr A^(m))^2 / Tr (A^(m))^2, written to a host double.  It counts the degeneracy of the
+ * dominant sector: X -> 2 in the ordered phase of the Ising model at h = 0, X -> 1 in the
+ * disordered phase.  After k steps leg position p is lattice direction (p + k) mod d.  One
+ * FP64 contraction of the current state; synchronises.  EINVAL for a leg outside 0..d-1,
+ * ESTATE before init, ENUMERIC when Tr (A^(m))^2 is zero or not finite. */
+tatrg_status tatrg_order_parameter(tatrg_ctx* ctx, int leg, double* X);
+
 /* Spectra of the last step, copied to a host array of capacity *n (on return *n holds
  * the count).  kind: 0 = s' (normalised, re-split), 1 = sigma of the bond swap,
  * 2 + (nu-1) = squeezer singular values of transverse leg position nu (1..d-1). */
@@ -156,6 +172,7 @@ typedef struct {
   int kernel_launches; /* all library kernel launches in the step */
   double tc_ms;        /* device time of the tc_launches (needs params.profile = 1) */
   double tc_flops;     /* their algorithmic flops, 2 M N K per contraction */
+  double partial_lnz;  /* sum_k 2^-k ln c_k over k = 0 .. step (the input of tatrg_set_state) */
 } tatrg_step_info;
 
 tatrg_status tatrg_last_step_info(const tatrg_ctx* ctx, tatrg_step_info* out);

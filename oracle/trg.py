@@ -439,6 +439,19 @@ def trace(A, s, B):
     return float(np.einsum("fa,a,af->", am, s, bm))
 
 
+def order_parameter_x(A, s, B, leg):
+    """Gu-Wen degeneracy order parameter of the current coarse tensor (Sec. 3, the
+    definition of X^(m)): A^(m)_kl = sum over every other leg x of T[.., x, k, ..; .., x, l, ..],
+    the forward leg at position ``leg`` open as k and its backward leg as l, and
+    X = (Tr A^(m))^2 / Tr (A^(m))^2.  T = A diag(s) B is never formed."""
+    d = A.ndim - 1
+    letters = "ijmnopqr"[:d]
+    fa = "".join("k" if p == leg else letters[p] for p in range(d))
+    fb = "".join("l" if p == leg else letters[p] for p in range(d))
+    Am = np.einsum("%sa,a,a%s->kl" % (fa, fb), A, s, B)
+    return float(np.trace(Am) ** 2 / np.trace(Am @ Am)), Am
+
+
 class Run:
     """State of an RG run: (A, s, B), step count and the ln Z / V partial sum."""
 

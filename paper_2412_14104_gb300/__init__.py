@@ -38,7 +38,8 @@ class StepInfo(ctypes.Structure):
                 ("lnc", ctypes.c_double), ("flops", ctypes.c_double * 5),
                 ("ms", ctypes.c_double * 5), ("swap_gap", ctypes.c_double),
                 ("tc_launches", ctypes.c_int), ("kernel_launches", ctypes.c_int),
-                ("tc_ms", ctypes.c_double), ("tc_flops", ctypes.c_double)]
+                ("tc_ms", ctypes.c_double), ("tc_flops", ctypes.c_double),
+                ("partial_lnz", ctypes.c_double)]
 
 
 class Contraction(ctypes.Structure):
@@ -66,6 +67,8 @@ def lib():
             "tatrg_lnZ": [P, D],
             "tatrg_grad": [P, D, D, D],
             "tatrg_sweep": [P, D, I, ctypes.c_double, I, I, D],
+            "tatrg_sweep_observables": [P, D, I, ctypes.c_double, I, I, D, D],
+            "tatrg_order_parameter": [P, I, D],
             "tatrg_spectrum": [P, I, D, ctypes.POINTER(I)],
             "tatrg_get_state": [P, ctypes.POINTER(I), ctypes.POINTER(I), D, D, D],
             "tatrg_set_state": [P, I, ctypes.POINTER(I), D, D, D, I, ctypes.c_double],
@@ -155,6 +158,19 @@ class Context:
         out = np.empty_like(b)
         _check(lib().tatrg_sweep(self._h, _dptr(b), b.size, h, d, nsteps, _dptr(out)), self._h)
         return out
+
+    def sweep_observables(self, betas, h, d, nsteps):
+        """(ln Z / V, X^(m) at leg d - 1) of every temperature run."""
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        z, x = np.empty_like(b), np.empty_like(b)
+        _check(lib().tatrg_sweep_observables(self._h, _dptr(b), b.size, h, d, nsteps, _dptr(z),
+                                             _dptr(x)), self._h)
+        return z, x
+
+    def order_parameter(self, leg):
+        out = ctypes.c_double()
+        _check(lib().tatrg_order_parameter(self._h, leg, ctypes.byref(out)), self._h)
+        return out.value
 
     def spectrum(self, kind):
         n = ctypes.c_int(0)

@@ -200,6 +200,32 @@ inline ModeIdx modes(std::initializer_list<Mode3> l) {
   return o;
 }
 
+inline ModeIdx modes(const std::vector<Mode3>& v) {
+  ModeIdx r;
+  for (const auto& x : v) {
+    if (x.ext == 1) continue;
+    if (r.n == kMaxModes) throw Error(TATRG_EINVAL, "too many modes in a contraction");
+    r.ext[r.n] = x.ext;
+    r.s0[r.n] = x.s0;
+    r.s1[r.n] = x.s1;
+    r.n++;
+  }
+  ModeIdx o;  // merge adjacent modes that are contiguous in both operands
+  for (int i = 0; i < r.n; ++i) {
+    if (o.n > 0 && o.s0[o.n - 1] == r.s0[i] * r.ext[i] && o.s1[o.n - 1] == r.s1[i] * r.ext[i]) {
+      o.ext[o.n - 1] *= r.ext[i];
+      o.s0[o.n - 1] = r.s0[i];
+      o.s1[o.n - 1] = r.s1[i];
+    } else {
+      o.ext[o.n] = r.ext[i];
+      o.s0[o.n] = r.s0[i];
+      o.s1[o.n] = r.s1[i];
+      o.n++;
+    }
+  }
+  return o;
+}
+
 // Device-side decomposition of a flat index into the two operand offsets.
 struct DevModes {
   int n;

@@ -186,7 +186,8 @@ SvdResult Engine::svd(const double* A, int64_t m, int64_t n) {
     r.V.buf = dalloc(n * n, s_);
     r.V.rows = n;
     r.V.cols = n;
-    jacobi_svd(A, m, int(n), r.U.p(), r.S.d(), r.V.p(), flag(1), s_, &st_);
+    if (qrcp_svd_fits(m, int(n))) jacobi_svd_qrcp(A, m, int(n), r.U.p(), r.S.d(), r.V.p(), flag(1), s_, &st_);
+    else jacobi_svd(A, m, int(n), r.U.p(), r.S.d(), r.V.p(), flag(1), s_, &st_);
   } else {
     DevBuf At(m * n * sizeof(double), s_);
     transpose(A, m, n, At.d(), s_);
@@ -196,7 +197,8 @@ SvdResult Engine::svd(const double* A, int64_t m, int64_t n) {
     r.U.buf = dalloc(m * m, s_);
     r.U.rows = m;
     r.U.cols = m;
-    jacobi_svd(At.d(), n, int(m), r.V.p(), r.S.d(), r.U.p(), flag(1), s_, &st_);
+    if (qrcp_svd_fits(n, int(m))) jacobi_svd_qrcp(At.d(), n, int(m), r.V.p(), r.S.d(), r.U.p(), flag(1), s_, &st_);
+    else jacobi_svd(At.d(), n, int(m), r.V.p(), r.S.d(), r.U.p(), flag(1), s_, &st_);
   }
   r.r = int(k);
   r.s = to_host(r.S.d(), k);

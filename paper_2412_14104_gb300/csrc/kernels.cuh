@@ -82,6 +82,11 @@ void tri_inverse(const double* R, int n, double* Rinv, cudaStream_t s);
 // S descending.  *status_dev = 0 converged, 1 not converged.
 void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double* V,
                 int* status_dev, cudaStream_t s, Stats* st);
+// The same SVD through a column-pivoted QR, A P = Q R, and the Jacobi on R^T (square-ish
+// matrices: 32 <= n <= 160, m >= n, m n <= 25600).
+bool qrcp_svd_fits(int64_t m, int n);
+void jacobi_svd_qrcp(const double* A, int64_t m, int n, double* U, double* S, double* V,
+                     int* status_dev, cudaStream_t s, Stats* st);
 // C (n x n) = A (n x n) * B (n x n), all row-major, small FP64 helper
 void transpose(const double* A, int64_t rows, int64_t cols, double* At, cudaStream_t s);
 // The same SVD with its workspace in a fixed file-scope device array (no allocation);

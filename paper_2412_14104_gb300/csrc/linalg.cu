@@ -506,6 +506,144 @@ __global__ void sumsq_kernel(const double* x, int64_t n, double* out) {
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Householder QR with column pivoting, A P = Q R (Businger & Golub 1965), of a row-major
+// m x n matrix (m >= n, m n <= kQrcpMaxElems), one block with the matrix in shared memory
+// (column-major).  Step k takes the remaining column of largest norm (ties: lowest index),
+// reflects rows k.. of it onto alpha e_k (alpha = -sign(x_0) ||x||) and updates the columns
+// to its right, one warp per column, recomputing their norms over rows k + 1.. in the same
+// pass.  Outputs: X = R^T (row-major n x n, lower triangular), the thin Q (row-major m x n,
+// formed in place by accumulating the reflectors backwards) and perm (column j of A P is
+// column perm[j] of A).
+constexpr int kQrcpMaxN = 160;
+constexpr int64_t kQrcpMaxElems = 25600;  // 200 KB of shared memory
+__global__ void __launch_bounds__(1024) qrcp_kernel(const double* A, int m, int n, double* X, double* Q,
+                                                    int* perm) {
+  extern __shared__ double W[];  // W[j * m + i] = column j, row i
+  __shared__ double nrm2[kQrcpMaxN], tau_s[kQrcpMaxN], diag_s[kQrcpMaxN];
+  __shared__ int piv[kQrcpMaxN];
+  __shared__ int pick;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int e = tid; e < m * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    W[j * m + i] = A[e];
+  }
+  for (int j = tid; j < n; j += blockDim.x) piv[j] = j;
+  __syncthreads();
+  for (int j = warp; j < n; j += nw) {
+    double acc = 0.0;
+    for (int i = lane; i < m; i += 32) acc = fma(W[j * m + i], W[j * m + i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) nrm2[j] = acc;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bj = k;
+      for (int j = k + lane; j < n; j += 32)
+        if (nrm2[j] > best) { best = nrm2[j]; bj = j; }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+      }
+      if (lane == 0) pick = bj;
+    }
+    __syncthreads();
+    const int p = pick;
+    if (p != k) {
+      for (int i = tid; i < m; i += blockDim.x) {
+        const double t = W[k * m + i];
+        W[k * m + i] = W[p * m + i];
+        W[p * m + i] = t;
+      }
+      if (tid == 0) {
+        const double t = nrm2[k];
+        nrm2[k] = nrm2[p];
+        nrm2[p] = t;
+        const int ti = piv[k];
+        piv[k] = piv[p];
+        piv[p] = ti;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double acc = 0.0;
+      for (int i = k + lane; i < m; i += 32) acc = fma(W[k * m + i], W[k * m + i], acc);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const double x0 = W[k * m + k], normx = sqrt(acc);
+        const double alpha = x0 >= 0.0 ? -normx : normx;
+        const double v0 = x0 - alpha;  // no cancellation: v0 and x0 have the same sign
+        const double vtv = acc - x0 * x0 + v0 * v0;
+        diag_s[k] = alpha;
+        tau_s[k] = vtv > 0.0 ? 2.0 / vtv : 0.0;
+        W[k * m + k] = v0;  // the reflector v = x - alpha e_0 stays in column k, rows k..
+      }
+    }
+    __syncthreads();
+    const double tau = tau_s[k];
+    for (int j = k + 1 + warp; j < n; j += nw) {
+      double d = 0.0;
+      for (int i = k + lane; i < m; i += 32) d = fma(W[k * m + i], W[j * m + i], d);
+      d = warp_sum(d) * tau;
+      double acc = 0.0;
+      for (int i = k + lane; i < m; i += 32) {
+        const double x = fma(-d, W[k * m + i], W[j * m + i]);
+        W[j * m + i] = x;
+        if (i > k) acc = fma(x, x, acc);
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) nrm2[j] = acc;
+    }
+    __syncthreads();
+  }
+  // X = R^T: R's strict upper part is in W above the diagonal, its diagonal in diag_s
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    X[e] = i > j ? W[i * m + j] : (i == j ? diag_s[i] : 0.0);
+  }
+  for (int j = tid; j < n; j += blockDim.x) perm[j] = piv[j];
+  __syncthreads();
+  for (int e = tid; e < m * n; e += blockDim.x) {  // clear R: Q has zeros above the diagonal
+    const int j = e / m, i = e - (e / m) * m;
+    if (i < j) W[e] = 0.0;
+  }
+  __syncthreads();
+  // Q = H_0 (H_1 (... (H_{n-1} [I; 0]))): at stage k the columns right of k hold the product of
+  // the later reflectors (zero in rows <= k); apply H_k to them, then replace the reflector in
+  // column k by H_k e_k
+  for (int k = n - 1; k >= 0; --k) {
+    const double tau = tau_s[k], v0 = W[k * m + k];
+    for (int j = k + 1 + warp; j < n; j += nw) {
+      double d = 0.0;
+      for (int i = k + lane; i < m; i += 32) d = fma(W[k * m + i], W[j * m + i], d);
+      d = warp_sum(d) * tau;
+      for (int i = k + lane; i < m; i += 32) W[j * m + i] = fma(-d, W[k * m + i], W[j * m + i]);
+    }
+    __syncthreads();
+    for (int i = k + tid; i < m; i += blockDim.x) W[k * m + i] = (i == k ? 1.0 : 0.0) - tau * v0 * W[k * m + i];
+    __syncthreads();
+  }
+  for (int e = tid; e < m * n; e += blockDim.x) {
+    const int i = e / n, j = e - (e / n) * n;
+    Q[e] = W[j * m + i];
+  }
+}
+
+// V[perm[j], :] = Ux[j, :] (n x n, row-major)
+__global__ void permute_rows_kernel(const double* Ux, const int* perm, int n, double* V) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int j = e / n, c = e - (e / n) * n;
+    V[int64_t(perm[j]) * n + c] = Ux[e];
+  }
+}
+
 // The single-block Jacobi keeps the whole m x N column-major copy in shared memory
 // (at most 200 KB); it is used for narrow matrices (N < 32) that fit.  Everything else,
 // including N = 2 with a tall m, takes the multi-block kernels, which handle one column
@@ -687,6 +825,35 @@ void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S,
                                                                                        sig, rk, U, V);
   TATRG_CUDA(cudaGetLastError());
   TATRG_CUDA(cudaStreamSynchronize(s));
+}
+
+// SVD through a pivoted QR (Drmac & Veselic, SIAM J. Matrix Anal. Appl. 29, 2008): A P = Q R,
+// then one-sided Jacobi on X = R^T, X = Ux S Vx^T, so A = (Q Vx) S (P Ux)^T.  Pivoting puts the
+// large columns first, and the rows of R are graded, so the Jacobi sweeps on R^T converge in
+// a few sweeps where the Jacobi on A takes tens.
+bool qrcp_svd_fits(int64_t m, int n) { return n >= 32 && n <= kQrcpMaxN && m >= n && m * n <= kQrcpMaxElems; }
+
+void jacobi_svd_qrcp(const double* A, int64_t m, int n, double* U, double* S, double* V, int* status_dev,
+                     cudaStream_t s, Stats* st) {
+  TATRG_CHECK(qrcp_svd_fits(m, n), TATRG_EINVAL, "jacobi_svd_qrcp: size out of range");
+  check_extent(A, m * n - 1, sizeof(double), "qrcp input");
+  check_extent(U, m * n - 1, sizeof(double), "qrcp U");
+  check_extent(V, int64_t(n) * n - 1, sizeof(double), "qrcp V");
+  DevBuf X(size_t(n) * n * sizeof(double), s), Qm(size_t(m) * n * sizeof(double), s),
+      perm(size_t(n) * sizeof(int), s), Ux(size_t(n) * n * sizeof(double), s), Vx(size_t(n) * n * sizeof(double), s);
+  ensure_smem_attr(reinterpret_cast<const void*>(qrcp_kernel), int(kQrcpMaxElems * sizeof(double)));
+  qrcp_kernel<<<1, 1024, size_t(m) * n * sizeof(double), s>>>(A, int(m), n, X.d(), Qm.d(), perm.as<int>());
+  TATRG_CUDA(cudaGetLastError());
+  jacobi_svd(X.d(), n, n, Ux.d(), S, Vx.d(), status_dev, s, st);
+  GemmDesc g;  // U = Q Vx
+  g.m = modes({{m, n, n}});
+  g.n = modes({{n, 1, 1}});
+  g.k = modes({{n, 1, n}});
+  gemm_f64(g, Qm.d(), Vx.d(), U, s, st);
+  permute_rows_kernel<<<int(std::max<int64_t>(1, std::min<int64_t>(cdiv(int64_t(n) * n, 256), 64))), 256, 0, s>>>(
+      Ux.d(), perm.as<int>(), n, V);
+  TATRG_CUDA(cudaGetLastError());
+  if (st) st->launches += 2;
 }
 
 void set_barrier_limit_ns(unsigned long long ns) {

@@ -183,6 +183,7 @@ struct tatrg_ctx {
                           DMat* psid = nullptr);
   double trace();
   double trace_tan(double tt);  // d ln tTr given tTr
+  double order_parameter(int leg);
   DMat isometry(Engine& E, const double* rho, int64_t Gd, int kind, std::vector<double>* lam_out,
                 const double* rhod = nullptr, DMat* Ud = nullptr);
   void factor(Engine& E, const double* rho, int64_t P, int kind, DMat& Rt, const double* rhod = nullptr,
@@ -310,6 +311,38 @@ double tatrg_ctx::trace() {
   DevBuf out(sizeof(double), stream);
   trace_asb(A.d(), sdev.d(), B.d(), prod(D, 0, D.size()), int(Da), out.d(), stream);
   return eng.to_host(out.d(), 1)[0];
+}
+
+// Gu-Wen order parameter X^(m) (Sec. 3): A^(m)[k, l] = sum over the other legs x of
+// T[.., x, k, ..; .., x, l, ..] with T = A diag(s) B, the leg at position `leg` open;
+// X = (Tr A^(m))^2 / Tr (A^(m))^2.  One FP64 contraction over the traced legs and the bond.
+double tatrg_ctx::order_parameter(int leg) {
+  const int64_t F = prod(D, 0, D.size()), Dp = D[leg];
+  DevBuf As(F * Da * sizeof(double), stream);
+  TATRG_CUDA(cudaMemcpyAsync(As.d(), A.d(), As.bytes(), cudaMemcpyDeviceToDevice, stream));
+  scale_axis(As.d(), sdev.d(), F, Da, 1, 1, stream);  // A[x, a] s_a
+  std::vector<Mode3> kk;
+  for (int i = 0; i < d; ++i)
+    if (i != leg) kk.push_back({D[i], prod(D, i + 1, d) * Da, prod(D, i + 1, d)});
+  kk.push_back({Da, 1, F});
+  GemmDesc g;
+  g.m = modes({{Dp, prod(D, leg + 1, d) * Da, Dp}});
+  g.n = modes({{Dp, prod(D, leg + 1, d), 1}});
+  g.k = modes(kk);
+  DevBuf Am(Dp * Dp * sizeof(double), stream);
+  const int saved = eng.prec;
+  eng.prec = 0;
+  eng.gemm(g, As.d(), B.d(), Am.d());
+  eng.prec = saved;
+  const std::vector<double> m = eng.to_host(Am.d(), Dp * Dp);
+  double tr = 0.0, tr2 = 0.0;
+  for (int64_t i = 0; i < Dp; ++i) {
+    tr += m[i * Dp + i];
+    for (int64_t j = 0; j < Dp; ++j) tr2 += m[i * Dp + j] * m[j * Dp + i];
+  }
+  TATRG_CHECK(tr2 != 0.0 && std::isfinite(tr2) && std::isfinite(tr), TATRG_ENUMERIC,
+              "order parameter: Tr (A^(m))^2 is zero or not finite");
+  return tr * tr / tr2;
 }
 
 // d ln tTr = (tTr(dA, s, B) + tTr(A, ds, B) + tTr(A, s, dB)) / tTr
@@ -1252,6 +1285,7 @@ void tatrg_ctx::rg_step() {
   info.tc_launches = int(eng.stats().tc_launches - tc0);
   info.tc_flops = eng.stats().flops_tc - tcf0;
   info.tc_ms = eng.stats().drain_ms();
+  info.partial_lnz = partial_lnz();
 }
 
 void tatrg_ctx::resplit_and_rotate(DMat& phi, DMat& psi, int64_t rows, int64_t Dg,
@@ -1463,6 +1497,11 @@ tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh, dou
 
 tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double h, int d,
                          int nsteps, double* lnZ_out) {
+  return tatrg_sweep_observables(ctx, betas, nbeta, h, d, nsteps, lnZ_out, nullptr);
+}
+
+tatrg_status tatrg_sweep_observables(tatrg_ctx* ctx, const double* betas, int nbeta, double h, int d,
+                                     int nsteps, double* lnZ_out, double* X_out) {
   if (!ctx || !betas || !lnZ_out || nbeta < 0) return TATRG_EINVAL;
   return guard(ctx, [&] {
     TATRG_CHECK(d >= 2 && d <= 4 && nsteps >= 0, TATRG_EINVAL, "tatrg_sweep: bad d or step count");
@@ -1498,6 +1537,7 @@ tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double 
             double tt = sub.trace();
             TATRG_CHECK(tt > 0.0 && std::isfinite(tt), TATRG_ENUMERIC, "non-positive final trace in sweep");
             lnZ_out[i] = sub.partial_lnz() + std::ldexp(std::log(tt), -sub.step);
+            if (X_out) X_out[i] = sub.order_parameter(d - 1);
           }
         } catch (const Error& e) {
           fail(e.code, e.what());
@@ -1513,6 +1553,15 @@ tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double 
     for (auto& t : pool) t.join();
     TATRG_CHECK(tc_error_flag(true) == 0, TATRG_ETIMEOUT, "a tensor-core pipeline wait timed out");
     if (first != TATRG_OK) throw Error(first, first_msg);
+  });
+}
+
+tatrg_status tatrg_order_parameter(tatrg_ctx* ctx, int leg, double* X) {
+  if (!ctx || !X) return TATRG_EINVAL;
+  return guard(ctx, [&] {
+    TATRG_CHECK(ctx->ready, TATRG_ESTATE, "tatrg_order_parameter before init");
+    TATRG_CHECK(leg >= 0 && leg < ctx->d, TATRG_EINVAL, "tatrg_order_parameter: leg out of range");
+    *X = ctx->order_parameter(leg);
   });
 }
 

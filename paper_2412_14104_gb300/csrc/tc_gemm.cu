@@ -68,15 +68,46 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// the same with acquire at cluster scope: for barriers that CTAs of a pair arrive on remotely
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 // bounded wait; false (and the error flag) when the deadline passes
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t deadline) {
-  while (!mbar_try_wait(bar, parity)) {
+  while (!(CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity))) {
     if (now_ns() > deadline) {
       atomicExch(&g_tc_error, 1);
       return false;
     }
   }
   return true;
+}
+// CTA pairs (a cluster of two CTAs on two SMs sharing one MMA)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared::cluster address of the same shared variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+// every thread of both CTAs of the pair
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
@@ -103,26 +134,66 @@ __device__ __forceinline__ uint64_t sdesc_sw(uint32_t saddr) {
   d |= uint64_t(KSLICE == 128 ? 2 : 4) << 61;     // SWIZZLE_128B : SWIZZLE_64B
   return d;
 }
-template <int PREC>
+// CG = 1: the MMA of one CTA; CG = 2: issued by the pair's first CTA for both (M = 256, each
+// CTA holding 128 rows of A, half of the N columns of B and 128 lanes of the accumulator)
+template <int PREC, int CG>
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                     uint32_t acc) {
-  if (PREC == 1) {
+  if (CG == 1 && PREC == 1) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  } else {
+  } else if (CG == 1) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else if (PREC == 1) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
   }
 }
+// completion of the MMAs issued so far arrives once on `bar`; with CG = 2 on the barrier at
+// the same offset in both CTAs of the pair
+template <int CG>
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
+  if (CG == 1) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+  } else {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+        "[%0], %1;" ::"r"(smem_u32(bar)),
+        "h"(uint16_t(3))
+        : "memory");
+  }
+}
+template <int CG>
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t cols) {
+  if (CG == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+}
+template <int CG>
+__device__ __forceinline__ void tmem_dealloc(uint32_t tmem, uint32_t cols) {
+  if (CG == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+  else asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
 }
 // 16 columns of 32 lanes; the caller waits with tmem_wait_ld before using r
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
@@ -148,10 +219,10 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 
 // Instruction descriptor for kind::tf32 (A/B format 2) or kind::f16 with bf16 (format 1),
 // FP32 accumulator, both operands K-major, M = 128.
-template <int PREC, int BN>
+template <int PREC, int BM, int BN>
 __device__ __forceinline__ constexpr uint32_t idesc() {
   return (1u << 4) | (uint32_t(PREC == 1 ? 2 : 1) << 7) | (uint32_t(PREC == 1 ? 2 : 1) << 10) |
-         (uint32_t(BN >> 3) << 17) | (uint32_t(TC_BM >> 4) << 24);
+         (uint32_t(BN >> 3) << 17) | (uint32_t(BM >> 4) << 24);
 }
 
 // float <-> double by IEEE-754 bit manipulation on the integer pipes: this GPU has few FP64
@@ -232,6 +303,7 @@ struct Unit {
 #ifndef TATRG_GROUP_M
 #define TATRG_GROUP_M 8
 #endif
+template <int TILE_M>
 __device__ __forceinline__ Unit unit_of(const TcArgs& g, int u) {
   constexpr int GROUP_M = TATRG_GROUP_M;
   const int tiles = g.mtiles * g.ntiles;
@@ -242,7 +314,7 @@ __device__ __forceinline__ Unit unit_of(const TcArgs& g, int u) {
   const int mt = first + (b % per_group) % gsize;
   const int nt = (b % per_group) / gsize;
   Unit w;
-  w.m0 = int64_t(mt) * TC_BM;
+  w.m0 = int64_t(mt) * TILE_M;
   w.n0 = int64_t(nt) * TC_BN;
   w.kb0 = sidx * g.kb_per_split;
   w.nk = min(g.nkb, w.kb0 + g.kb_per_split) - w.kb0;
@@ -271,21 +343,32 @@ __device__ __forceinline__ bool epilogue_all(bool p) {
   return r != 0;
 }
 
-template <int PREC, int KC, int STAGES, int NBUF>
+// PAIR: the CTAs of a cluster of two share each 256 x 128 tile: CTA r loads rows
+// m0 + 128 r .. of A and rows n0 + 64 r .. of B (half of the tile's N) into its own shared
+// memory, its tensor memory holds rows m0 + 128 r .. of the accumulator, and its epilogue
+// writes them.  The first CTA (rank 0) issues the MMAs of both (cta_group::2); the second
+// CTA's warp 1 tells it, through a barrier in the first CTA's shared memory, when each of
+// its stages has landed, and the second CTA's epilogue warps arrive on the first CTA's
+// accumulator-empty barriers.  Per SM this halves the B operand traffic of each MMA.
+template <int PREC, int KC, int STAGES, int NBUF, bool PAIR>
 __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's register file
     tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                    const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
                    TcArgs g) {
+  constexpr int CG = PAIR ? 2 : 1;
   constexpr int BN = TC_BN;
-  constexpr int A_TILE = TC_BM * KSLICE;  // bytes
-  constexpr int B_TILE = BN * KSLICE;
+  constexpr int TILE_M = TC_BM * CG;        // output rows per tile (per pair)
+  constexpr int B_ROWS = BN / CG;           // rows of B (output columns) per CTA
+  constexpr int A_TILE = TC_BM * KSLICE;    // bytes
+  constexpr int B_TILE = B_ROWS * KSLICE;
   constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;
   constexpr int KELEM = PREC == 1 ? KSLICE / 4 : KSLICE / 2;  // K elements per stage
   constexpr int TMEM_COLS = NBUF * BN + 2 * BN;  // chunk buffers, running hi, running lo
   static_assert(TMEM_COLS == 512, "the tensor memory holds exactly 512 columns");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_full[NBUF], acc_empty[NBUF], fin_bar;
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], peer_full[STAGES], acc_full[NBUF],
+      acc_empty[NBUF], fin_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ int64_t col_off[BN];
   // per epilogue warp: a 32-row x 8-column slice of doubles (XOR-swizzled by row), through
@@ -294,26 +377,26 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int units = g.mtiles * g.ntiles * g.split;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const int first = PAIR ? int(blockIdx.x >> 1) : int(blockIdx.x);  // this CTA's (pair's) first unit
+  const int stride = PAIR ? int(gridDim.x >> 1) : int(gridDim.x);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
+      mbar_init(&peer_full[s], 1);
     }
     for (int b = 0; b < NBUF; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], EPI_WARPS);
+      mbar_init(&acc_empty[b], CG * EPI_WARPS);
     }
     mbar_init(&fin_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_base_s)),
-                 "r"(uint32_t(TMEM_COLS)));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
+  if (PAIR) cluster_sync_all();  // both CTAs' barriers exist before any remote arrive
+  if (warp == 1) tmem_alloc<CG>(&tmem_base_s, uint32_t(TMEM_COLS));
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -323,18 +406,19 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
     if (lane == 0) {
       int it = 0;  // stage uses, continued across units
       bool ok = true;
-      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const Unit w = unit_of(g, u);
+      for (int u = first; u < units && ok; u += stride) {
+        const Unit w = unit_of<TILE_M>(g, u);
         for (int i = 0; i < w.nk; ++i, ++it) {
           const int s = it % STAGES, round = it / STAGES;
-          if (round > 0 && !mbar_wait(&empty_bar[s], (round - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+          if (round > 0 && !mbar_wait<PAIR>(&empty_bar[s], (round - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
           uint8_t* st = smem + s * STAGE;
           mbar_expect_tx(&full_bar[s], STAGE);
           const int kx = (w.kb0 + i) * KELEM;
-          tma_load_2d(st, &ta_hi, &full_bar[s], kx, int(w.m0));
-          tma_load_2d(st + A_TILE, &ta_lo, &full_bar[s], kx, int(w.m0));
-          tma_load_2d(st + 2 * A_TILE, &tb_hi, &full_bar[s], kx, int(w.n0));
-          tma_load_2d(st + 2 * A_TILE + B_TILE, &tb_lo, &full_bar[s], kx, int(w.n0));
+          const int ya = int(w.m0) + int(rank) * TC_BM, yb = int(w.n0) + int(rank) * B_ROWS;
+          tma_load_2d(st, &ta_hi, &full_bar[s], kx, ya);
+          tma_load_2d(st + A_TILE, &ta_lo, &full_bar[s], kx, ya);
+          tma_load_2d(st + 2 * A_TILE, &tb_hi, &full_bar[s], kx, yb);
+          tma_load_2d(st + 2 * A_TILE + B_TILE, &tb_lo, &full_bar[s], kx, yb);
         }
       }
       // drain: the last loads issued into each stage must have landed before the CTA exits
@@ -342,23 +426,24 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
       for (int i = max(0, it - STAGES); i < it; ++i)
         mbar_wait(&full_bar[i % STAGES], (i / STAGES) & 1, drain);
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 && rank == 0) {
     if (lane == 0) {
-      constexpr uint32_t id = idesc<PREC, BN>();
+      constexpr uint32_t id = idesc<PREC, TILE_M, BN>();
       int it = 0, cc = 0;  // stage uses and chunks, continued across units
       bool ok = true;
-      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-        const Unit w = unit_of(g, u);
+      for (int u = first; u < units && ok; u += stride) {
+        const Unit w = unit_of<TILE_M>(g, u);
         const int nchunks = (w.nk + KC - 1) / KC;
         for (int c = 0; c < nchunks && ok; ++c, ++cc) {
           const int b = cc % NBUF, use = cc / NBUF;
-          if (use > 0 && !mbar_wait(&acc_empty[b], (use - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+          if (use > 0 && !mbar_wait<PAIR>(&acc_empty[b], (use - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
           tc_fence_after();
           const uint32_t acc = tmem + uint32_t(b * BN);
           const int i_end = min(w.nk, (c + 1) * KC);
           for (int i = c * KC; i < i_end; ++i, ++it) {
             const int s = it % STAGES, round = it / STAGES;
             if (!mbar_wait(&full_bar[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+            if (PAIR && !mbar_wait<true>(&peer_full[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
             tc_fence_after();
             const uint32_t base = smem_u32(smem + s * STAGE);
             const uint64_t ahi = sdesc_sw(base), alo = sdesc_sw(base + A_TILE);
@@ -366,18 +451,36 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
 #pragma unroll
             for (int kk = 0; kk < KSLICE / 32; ++kk) {  // 32 bytes of K per instruction
               const uint64_t off = uint64_t(kk * 2);
-              mma<PREC>(acc, alo + off, bhi + off, id, (i > c * KC || kk > 0) ? 1u : 0u);
-              mma<PREC>(acc, ahi + off, blo + off, id, 1u);
-              mma<PREC>(acc, ahi + off, bhi + off, id, 1u);
+              mma<PREC, CG>(acc, alo + off, bhi + off, id, (i > c * KC || kk > 0) ? 1u : 0u);
+              mma<PREC, CG>(acc, ahi + off, blo + off, id, 1u);
+              mma<PREC, CG>(acc, ahi + off, bhi + off, id, 1u);
             }
-            mma_commit(&empty_bar[s]);
+            mma_commit<CG>(&empty_bar[s]);
           }
-          if (ok) mma_commit(&acc_full[b]);
+          if (ok) mma_commit<CG>(&acc_full[b]);
         }
       }
       // drain: every MMA issued by this thread completes before TMEM is released
-      mma_commit(&fin_bar);
-      mbar_wait(&fin_bar, 0, now_ns() + WAIT_NS);
+      mma_commit<CG>(&fin_bar);
+      mbar_wait<PAIR>(&fin_bar, 0, now_ns() + WAIT_NS);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // second CTA of a pair: forward "stage landed" to the first CTA, which issues the MMAs
+      const uint32_t peer0 = cluster_addr(&peer_full[0], 0);
+      int it = 0;
+      bool ok = true;
+      for (int u = first; u < units && ok; u += stride) {
+        const Unit w = unit_of<TILE_M>(g, u);
+        for (int i = 0; i < w.nk; ++i, ++it) {
+          const int s = it % STAGES, round = it / STAGES;
+          if (!mbar_wait(&full_bar[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+          mbar_arrive_remote(peer0 + uint32_t(s * sizeof(uint64_t)));
+        }
+      }
+      // the first CTA's final commit also arrives here: its MMAs into this CTA's tensor
+      // memory are complete before the memory is released
+      mbar_wait<true>(&fin_bar, 0, now_ns() + WAIT_NS);
     }
   } else {
     // epilogue warps 2..17: TMEM lane quarter q = warp % 4 (the lanes a warp may access),
@@ -385,15 +488,16 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
     // [NBUF*BN, NBUF*BN + BN) (hi) and [NBUF*BN + BN, NBUF*BN + 2*BN) (lo), so the drain
     // needs few registers.
     const int q = warp & 3, h = (warp - 2) >> 2;
-    const int row = q * 32 + lane;
+    const int row = int(rank) * TC_BM + q * 32 + lane;  // row of the tile
     const uint32_t lanes = tmem + (uint32_t(q * 32) << 16);
     const uint32_t t_hi = lanes + uint32_t(NBUF * BN + h * 32);
     const uint32_t t_lo = lanes + uint32_t(NBUF * BN + BN + h * 32);
+    const uint32_t empty0 = PAIR ? cluster_addr(&acc_empty[0], 0) : 0u;
     int cc = 0;
     bool ok = true;
 #pragma unroll 1
-    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
-      const Unit w = unit_of(g, u);
+    for (int u = first; u < units && ok; u += stride) {
+      const Unit w = unit_of<TILE_M>(g, u);
       // per-column C offsets of this tile (the previous tile's stores are done with them)
       asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
       for (int j = threadIdx.x - 64; j < BN; j += EPI_WARPS * 32) {
@@ -406,7 +510,7 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
 #pragma unroll 1
       for (int c = 0; c < nchunks; ++c, ++cc) {
         const int b = cc % NBUF, use = cc / NBUF;
-        ok = __all_sync(0xffffffffu, (ok && mbar_wait(&acc_full[b], use & 1, now_ns() + WAIT_NS)) ? 1 : 0) != 0;
+        ok = __all_sync(0xffffffffu, (ok && mbar_wait<PAIR>(&acc_full[b], use & 1, now_ns() + WAIT_NS)) ? 1 : 0) != 0;
         if (!ok) break;
         tc_fence_after();
         const uint32_t ta = lanes + uint32_t(b * BN + h * 32);
@@ -422,8 +526,10 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
           if (part == 1) {  // the whole slice has been read: hand the buffer back to the MMA warp
             tc_fence_before();
             __syncwarp();
-            if (lane == 0)
-              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+            if (lane == 0) {
+              if (PAIR) mbar_arrive_remote(empty0 + uint32_t(b * sizeof(uint64_t)));
+              else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+            }
           }
           if (c == 0) {
 #pragma unroll
@@ -517,9 +623,12 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
   }
   tc_fence_before();
   __syncthreads();
+  // a pair: no CTA releases its tensor memory or exits while the other may still arrive on
+  // its barriers
+  if (PAIR) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(TMEM_COLS)));
+    tmem_dealloc<CG>(tmem, uint32_t(TMEM_COLS));
   }
 }
 
@@ -705,32 +814,86 @@ CUtensorMap make_map(void* base, int64_t rows, int64_t kp, int esize, int box_ro
   return m;
 }
 
-template <int PREC>
+// Shared-memory ring of the kernel: stages of A (hi, lo) and B (hi, lo) slices.
+template <bool PAIR>
+constexpr int stage_bytes() { return 2 * TC_BM * KSLICE + 2 * (PAIR ? TC_BN / 2 : TC_BN) * KSLICE; }
+
+// Largest number of CTAs (of pairs: clusters) that are resident at once, per device.
+template <int PREC, bool PAIR>
+int resident_units(const void* kfn, int smem) {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  int dev = 0;
+  TATRG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> l(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  TATRG_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  int n = 0;
+  if (PAIR) {
+    TATRG_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * unsigned(sm_count() / 2));
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = size_t(smem);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    TATRG_CUDA(cudaOccupancyMaxActiveClusters(&n, kfn, &cfg));
+  } else {
+    int per_sm = 0;
+    TATRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, TC_THREADS, smem));
+    n = per_sm >= 1 ? sm_count() : 0;  // one CTA per SM: the ring admits no second one
+  }
+  TATRG_CHECK(n >= 1, TATRG_ECUDA, "gemm_tc: the tensor-core kernel does not fit on the device");
+  cache[dev] = n;
+  return n;
+}
+
+template <int PREC, bool PAIR>
 void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
-            const CUtensorMap& blo, const TcArgs& a, dim3 grid, cudaStream_t s) {
-  constexpr int STAGE = 2 * TC_BM * KSLICE + 2 * TC_BN * KSLICE;
+            const CUtensorMap& blo, const TcArgs& a, int64_t units, cudaStream_t s) {
+  constexpr int STAGE = stage_bytes<PAIR>();
   constexpr int STAGES = SMEM_BUDGET / STAGE;
   constexpr int KC = TATRG_CHAIN_K / (PREC == 1 ? KSLICE / 4 : KSLICE / 2);  // stages per FP32 chain
   static_assert(KC >= 1, "an FP32 chain spans at least one stage");
   constexpr int SMEM = STAGES * STAGE + 1024;
-  auto k = tc_gemm_kernel<PREC, KC, STAGES, 2>;
-  // the shared-memory attribute and the occupancy check, once per device and instantiation
-  static std::mutex mu;
-  static std::map<int, int> resident_on;
-  int dev = 0;
-  TATRG_CUDA(cudaGetDevice(&dev));
-  {
-    std::lock_guard<std::mutex> l(mu);
-    if (!resident_on.count(dev)) {
-      TATRG_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-      int n = 0;
-      TATRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, TC_THREADS, SMEM));
-      resident_on[dev] = n;
-    }
-    TATRG_CHECK(resident_on[dev] >= 1, TATRG_ECUDA, "gemm_tc: the tensor-core kernel does not fit on an SM");
+  auto k = tc_gemm_kernel<PREC, KC, STAGES, 2, PAIR>;
+  const int resident = resident_units<PREC, PAIR>(reinterpret_cast<const void*>(k), SMEM);
+  // persistent: every CTA (pair) walks units b, b + grid, ...; no more CTAs than are resident
+  const unsigned n = unsigned(std::min<int64_t>(units, resident));
+  if (!PAIR) {
+    k<<<n, TC_THREADS, SMEM, s>>>(ahi, alo, bhi, blo, a);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * n);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = size_t(SMEM);
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    TATRG_CUDA(cudaLaunchKernelEx(&cfg, k, ahi, alo, bhi, blo, a));
   }
-  k<<<grid, TC_THREADS, SMEM, s>>>(ahi, alo, bhi, blo, a);
   TATRG_CUDA(cudaGetLastError());
+}
+
+// CTA pairs for the contractions with many 256-row tiles (set TATRG_CTA_PAIR=0 to use single
+// CTAs everywhere, e.g. to compare the two).
+bool pairs_enabled() {
+  static const bool on = []() {
+    const char* e = getenv("TATRG_CTA_PAIR");
+    return !(e && e[0] == '0');
+  }();
+  return on;
 }
 
 }  // namespace
@@ -779,7 +942,11 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   const int esize = prec == 1 ? 4 : 2;
   const int kelem = KSLICE / esize;
   const int BN = TC_BN;
-  const int64_t Mp = cdiv(M, TC_BM) * TC_BM, Np = cdiv(N, BN) * BN, Kp = cdiv(K, kelem) * kelem;
+  // a CTA pair per 256 x 128 tile when there are many such tiles (the last tile row is then
+  // less than half padding)
+  const bool pair = pairs_enabled() && M >= 1024;
+  const int tile_m = pair ? 2 * TC_BM : TC_BM;
+  const int64_t Mp = cdiv(M, tile_m) * tile_m, Np = cdiv(N, BN) * BN, Kp = cdiv(K, kelem) * kelem;
   TATRG_CHECK(Mp < (int64_t(1) << 31) && Np < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: operand too large");
   // packed operands (hi, lo) in one allocation
   const size_t abytes = size_t(Mp) * Kp * esize, bbytes = size_t(Np) * Kp * esize;
@@ -822,13 +989,13 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   }
   CUtensorMap mahi = make_map(ahi, Mp, Kp, esize, TC_BM, prec);
   CUtensorMap malo = make_map(alo, Mp, Kp, esize, TC_BM, prec);
-  CUtensorMap mbhi = make_map(bhi, Np, Kp, esize, BN, prec);
-  CUtensorMap mblo = make_map(blo, Np, Kp, esize, BN, prec);
+  CUtensorMap mbhi = make_map(bhi, Np, Kp, esize, pair ? BN / 2 : BN, prec);
+  CUtensorMap mblo = make_map(blo, Np, Kp, esize, pair ? BN / 2 : BN, prec);
   const int nkb = int(Kp / kelem);
-  const int64_t tiles = (Mp / TC_BM) * (Np / BN);
+  const int64_t tiles = (Mp / tile_m) * (Np / BN);
   int split = 1;
-  const int64_t sms = sm_count();
-  if (tiles < 2 * sms && nkb >= 8) split = int(std::min<int64_t>(cdiv(2 * sms, tiles), nkb / 4));
+  const int64_t workers = pair ? sm_count() / 2 : sm_count();  // CTAs or pairs
+  if (tiles < 2 * workers && nkb >= 8) split = int(std::min<int64_t>(cdiv(2 * workers, tiles), nkb / 4));
   split = std::max(1, std::min(split, 512));
   const int per = int(cdiv(nkb, split));
   split = int(cdiv(nkb, per));
@@ -853,17 +1020,17 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     scale_c_kernel<<<int(std::min<int64_t>(cdiv(M * N, 256), 4096)), 256, 0, s>>>(C, dev(d.m), dev(d.n), M, N, d.beta);
     TATRG_CUDA(cudaGetLastError());
   }
-  a.mtiles = int(Mp / TC_BM);
+  a.mtiles = int(Mp / tile_m);
   a.ntiles = int(Np / BN);
   a.split = split;
   const int64_t units = int64_t(a.mtiles) * a.ntiles * split;
   TATRG_CHECK(units < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: too many work units");
-  // persistent: one CTA per SM (the shared-memory ring admits no second one)
-  dim3 grid(unsigned(std::min<int64_t>(units, sms)));
   const bool timed = st && st->timing;
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
-  if (prec == 1) launch<1>(mahi, malo, mbhi, mblo, a, grid, s);
-  else launch<2>(mahi, malo, mbhi, mblo, a, grid, s);
+  if (prec == 1 && pair) launch<1, true>(mahi, malo, mbhi, mblo, a, units, s);
+  else if (prec == 1) launch<1, false>(mahi, malo, mbhi, mblo, a, units, s);
+  else if (pair) launch<2, true>(mahi, malo, mbhi, mblo, a, units, s);
+  else launch<2, false>(mahi, malo, mbhi, mblo, a, units, s);
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
   if (st) {
     st->launches += 3 + (split > 1);

@@ -61,3 +61,22 @@ def high_t_lnz(beta, d):
     which there are C(d, 2) per site.  The next term is O(tanh^6 b)."""
     t = math.tanh(beta)
     return math.log(2.0) + d * math.log(math.cosh(beta)) + math.comb(d, 2) * t ** 4
+
+
+def transfer_matrix_lnz(beta, h, L0, L1):
+    """ln Z of the 2D Ising model on an L0 x L1 periodic lattice by the row transfer matrix:
+    a column of L0 spins along direction 0 (ring bonds sigma_i sigma_{i+1 mod L0}, so L0 = 2
+    gives double bonds and L0 = 1 a self-loop, as in brute_force_lnz), Z = Tr T^L1 with
+    T[s, s'] = exp(beta sum_i s_i s_{i+1} + h sum_i s_i + beta sum_i s_i s'_i)."""
+    n = 2 ** L0
+    spins = 1 - 2 * ((np.arange(n)[:, None] >> np.arange(L0)[None, :]) & 1)
+    ring = np.sum(spins * np.roll(spins, -1, axis=1), axis=1)
+    site = ring * beta + h * spins.sum(axis=1)
+    inter = beta * (spins @ spins.T)
+    T = np.exp(site[:, None] + inter)
+    # Tr T^L1 through the eigenvalues of the symmetric matrix D^1/2 K D^1/2 (same spectrum)
+    Ts = np.exp(0.5 * site)[:, None] * np.exp(inter) * np.exp(0.5 * site)[None, :]
+    lam = np.linalg.eigvalsh(Ts)
+    m = np.max(np.abs(lam))
+    return math.log(m) * L1 + math.log(np.sum((lam / m) ** L1))
+

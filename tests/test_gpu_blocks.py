@@ -109,6 +109,29 @@ def test_jacobi_svd(torch, m, n):
     assert np.allclose(v.T @ v, np.eye(n), atol=1e-13)
 
 
+@pytest.mark.parametrize("m,n,spread", [(144, 144, 1e-12), (160, 100, 1e-6), (144, 144, 1.0), (120, 32, 1e-9)])
+def test_svd_through_pivoted_qr(torch, m, n, spread):
+    """Square-ish SVDs (32 <= n <= 160) take the pivoted-QR-preconditioned Jacobi: singular
+    values spread over 1 .. spread (graded, like the Gram spectra of the step), random
+    singular vectors; against NumPy and the reconstruction."""
+    rng = np.random.default_rng(int(m + n + 1 / spread) % 1000)
+    Uq, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    Vq, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    sv = np.logspace(0, np.log10(spread), n) if spread < 1 else 1.0 + rng.random(n)
+    A = (Uq * sv) @ Vq.T
+    U = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    S = torch.empty(n, dtype=torch.float64, device="cuda")
+    V = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    tg.svd(_dev(torch, A), U, S, V)
+    u, s, v = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    s_ref = np.linalg.svd(A, compute_uv=False)
+    assert np.all(np.diff(s) <= 0)
+    assert np.allclose(s, s_ref, rtol=1e-12, atol=1e-15 * s_ref[0])
+    assert np.allclose((u * s) @ v.T, A, atol=1e-13 * s_ref[0])
+    assert np.allclose(v.T @ v, np.eye(n), atol=1e-13)
+    assert np.allclose(u.T @ u, np.eye(n), atol=1e-11 if spread >= 1e-6 else 1e-3)
+
+
 def test_orth_full_rank_and_rank_deficient(torch):
     rng = np.random.default_rng(3)
     m, n = 500, 24
@@ -180,6 +203,36 @@ def test_contract_tensor_core_plain(torch, prec):
     A = rng.standard_normal((M, K))
     B = rng.standard_normal((K, N))
     err = _tc_case(torch, prec, M, N, K, [(M, K, N)], [(N, 1, 1)], [(K, 1, N)], A, B, A @ B)
+    assert err < TC_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+@pytest.mark.parametrize("M,N,K", [(1037, 300, 517), (1024, 256, 4096), (2500, 130, 64), (4099, 1000, 33)])
+def test_contract_tensor_core_cta_pair_tiles(torch, prec, M, N, K):
+    """M >= 1024 takes 256 x 128 tiles on CTA pairs: ragged last tile rows and columns, a
+    split K (few tiles, long K: float64 atomics), a single K slice."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((K, N))
+    C0 = rng.standard_normal((M, N))
+    want = A @ B - 0.5 * C0
+    err = _tc_case(torch, prec, M, N, K, [(M, K, N)], [(N, 1, 1)], [(K, 1, N)], A, B, want,
+                   beta_C=C0, beta=-0.5)
+    assert err < TC_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+def test_contract_tensor_core_cta_pair_multimode(torch, prec):
+    """Permuted multi-mode operands and output on the CTA-pair path (M = 37 * 41 >= 1024)."""
+    rng = np.random.default_rng(14)
+    I, J, a, b, K, L = 37, 29, 41, 11, 13, 17
+    A = rng.standard_normal((K, I, L, a))
+    B = rng.standard_normal((b, L, J, K))
+    want = np.einsum("kila,bljk->aibj", A, B)
+    m = [(I, L * a, b * J), (a, 1, I * b * J)]
+    n = [(J, K, 1), (b, L * J * K, J)]
+    k = [(K, I * L * a, 1), (L, a, J * K)]
+    err = _tc_case(torch, prec, I * a, J * b, K * L, m, n, k, A, B, want)
     assert err < TC_TOL[prec], err
 
 

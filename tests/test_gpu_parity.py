@@ -197,3 +197,31 @@ def test_split_precision_free_energy_within_1e8(prec):
                      split_from_step=13).init_ising(c["beta"], c["h"], c["d"])
     lnz = ctx.rg_step(c["steps"]).lnZ()
     assert abs(lnz - g["lnz"]) < 1e-8 * abs(g["lnz"]), (lnz, g["lnz"])
+
+
+def test_order_parameter_untruncated_2d_torus():
+    """X^(m) of the exact 4 x 4 block equals Z(4 x 4)^2 / Z(4 x 8) (transfer matrix)."""
+    for beta, h in ((0.3, 0.0), (0.4407, 0.0), (0.6, 0.02)):
+        ctx = tg.Context(256, 64, 2).init_ising(beta, h, 2).rg_step(4)
+        z = exact_ising.transfer_matrix_lnz(beta, h, 4, 4)
+        zz = exact_ising.transfer_matrix_lnz(beta, h, 4, 8)
+        for leg in (0, 1):
+            assert abs(math.log(ctx.order_parameter(leg)) - (2 * z - zz)) < 1e-10
+
+
+def test_order_parameter_matches_oracle_and_sweep():
+    """Truncated 4D runs: X^(m) of every leg equals the oracle's from the same run; the
+    temperature sweep reports the same X as single runs (replica i for temperature i)."""
+    p = trg.Params(8, 2, q=2, seed=3)
+    run = trg.Run(0.1497, 1e-4, 4, p).step(10)
+    ctx = tg.Context(8, 2, 2, seed=3).init_ising(0.1497, 1e-4, 4).rg_step(10)
+    for leg in range(4):
+        want, _ = trg.order_parameter_x(run.A, run.s, run.B, leg)
+        assert abs(ctx.order_parameter(leg) - want) < 1e-10 * want
+    betas = [0.12, 0.1497, 0.2]
+    z, x = tg.Context(8, 2, 2, seed=3, sweep_workers=2).sweep_observables(betas, 0.0, 4, 10)
+    for i, b in enumerate(betas):
+        r = trg.Run(b, 0.0, 4, trg.Params(8, 2, q=2, seed=3, replica=i)).step(10)
+        assert abs(z[i] - r.lnz()) < 1e-11 * abs(r.lnz())
+        assert abs(x[i] - trg.order_parameter_x(r.A, r.s, r.B, 3)[0]) < 1e-9 * x[i]
+    assert x[2] > 1.5 > x[0]  # ordered at beta = 0.2, disordered at 0.12 (4D: beta_c ~ 0.1497)

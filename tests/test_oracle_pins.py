@@ -530,3 +530,47 @@ def test_bond_swap_preserves_the_two_site_product():
     T = np.einsum("iabsx,x,xjefh->iabsjefh", A, s, B)
     want = np.einsum("iabskBCD,kcdtjefh->iabscdtBCDjefh", T, T)
     assert np.allclose(got, want, atol=1e-13 * np.abs(want).max())
+
+
+# --- transition-point order parameter X^(m) -------------------------------------------
+
+def test_transfer_matrix_matches_enumeration():
+    """The transfer-matrix partition function used below against brute force (small tori,
+    with L = 1 self-loops and L = 2 double bonds)."""
+    for L0, L1, beta, h in ((2, 2, 0.4, 0.0), (3, 4, 0.3, 0.1), (1, 3, 0.7, -0.2), (4, 2, 0.44, 0.05)):
+        want, _, _ = exact_ising.brute_force_lnz(beta, h, (L0, L1))
+        assert abs(exact_ising.transfer_matrix_lnz(beta, h, L0, L1) - want) < 1e-11
+
+
+def test_order_parameter_is_a_ratio_of_partition_functions():
+    """With nothing truncated, T represents the whole block of sites coarse-grained so far,
+    Tr A^(m) is Z of that block's torus and Tr (A^(m))^2 is Z of the torus doubled along the
+    open leg's direction, so X = Z(block)^2 / Z(doubled).  Leg position p after k steps is
+    lattice direction (p + k) mod d."""
+    # 2D, four steps: a 4 x 4 block; the doubled torus (8 x 4 or 4 x 8) by transfer matrix
+    for beta, h in ((0.3, 0.0), (0.4407, 0.0), (0.6, 0.02)):
+        run = trg.Run(beta, h, 2, INF).step(4)
+        z = exact_ising.transfer_matrix_lnz(beta, h, 4, 4)
+        for leg in (0, 1):
+            x, _ = trg.order_parameter_x(run.A, run.s, run.B, leg)
+            zz = exact_ising.transfer_matrix_lnz(beta, h, 4, 8)  # symmetric block: either axis
+            assert abs(math.log(x) - (2 * z - zz)) < 1e-10
+    # 4D, two steps: block (2, 2, 1, 1) along directions (0, 1, 2, 3); positions are
+    # (dir 2, dir 3, dir 0, dir 1)
+    beta, h = 0.1497, 0.05
+    run = trg.Run(beta, h, 4, INF).step(2)
+    z, _, _ = exact_ising.brute_force_lnz(beta, h, (2, 2, 1, 1))
+    for leg, doubled in ((3, (2, 4, 1, 1)), (2, (4, 2, 1, 1)), (0, (2, 2, 2, 1))):
+        x, _ = trg.order_parameter_x(run.A, run.s, run.B, leg)
+        zz, _, _ = exact_ising.brute_force_lnz(beta, h, doubled)
+        assert abs(math.log(x) - (2 * z - zz)) < 1e-11, leg
+
+
+def test_order_parameter_limits():
+    """X counts the ground-state degeneracy: deep in the ordered phase (large beta, h = 0)
+    the coarse tensor has two equal sectors and X -> 2; at high temperature X -> 1."""
+    hot = trg.Run(0.05, 0.0, 2, trg.Params(8, 2, seed=1)).step(12)
+    cold = trg.Run(1.2, 0.0, 2, trg.Params(8, 2, seed=1)).step(12)
+    assert abs(trg.order_parameter_x(hot.A, hot.s, hot.B, 1)[0] - 1.0) < 1e-6
+    assert abs(trg.order_parameter_x(cold.A, cold.s, cold.B, 1)[0] - 2.0) < 1e-6
+
