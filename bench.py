@@ -273,7 +273,7 @@ def run_c3(args):
     import paper_2412_14104_gb300 as tg
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    prec_of = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "fp64": tg.FP64}
+    prec_of = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}
     forms = [parse_form(f) for f in args.c3_forms.split(",")]
     branch_at = sorted({k for name, k in forms if name != "fp64" and k > 1})
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -347,6 +347,206 @@ def c3_summary(out):
                       for k, v in runs.items()}}
 
 
+METHODS_FILE = os.path.join(ROOT, "profiles", "methods_scaling.json")
+
+
+def run_methods(args):
+    """Triad-ATRG against plain ATRG (the triad with identity isometries, the O(chi^9)
+    contraction) in the paper's comparison setting r = 7 (Table 2, Figs. 5 and 6): for each
+    chi of --methods-chis, the steady-state step time (CUDA events over --steps steps after
+    the legs reach chi) and ln Z / V after --methods-steps steps, at beta = 0.1497, h = 0,
+    d = 4, in the precision of --precision.  Writes profiles/methods_scaling.json with a
+    least-squares exponent of step time against chi per method; prints one JSON line."""
+    import numpy as np
+    import torch
+    import paper_2412_14104_gb300 as tg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}[args.precision]
+    chis = [int(c) for c in args.methods_chis.split(",")]
+    r = 7
+    rows = {}
+    for method, mname in ((tg.TRIAD, "triad"), (tg.ATRG, "atrg")):
+        for chi in chis:
+            ctx = tg.Context(chi, r, Q, method=method, seed=SEED, precision=prec, stream=stream)
+            ctx.init_ising(BETA, 0.0, 4)
+            k = 0
+            while not all(x == chi for x in list(ctx.step_info().dims)[:5]) or k == 0:
+                ctx.rg_step()
+                k += 1
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.rg_step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            k += args.steps
+            ms = e0.elapsed_time(e1) / args.steps
+            if args.methods_steps > k:
+                ctx.rg_step(args.methods_steps - k)
+            lnz = ctx.lnZ()
+            ctx.close()
+            rows["%s_%d" % (mname, chi)] = {"method": mname, "chi": chi, "r": r, "ms_per_step": ms,
+                                             "lnz": lnz, "steps": max(k, args.methods_steps)}
+            print("%s chi=%d: %.1f ms/step, lnZ/V %.12f" % (mname, chi, ms, lnz), flush=True)
+    fits = {}
+    for mname in ("triad", "atrg"):
+        pts = [(math.log(v["chi"]), math.log(v["ms_per_step"])) for v in rows.values() if v["method"] == mname]
+        if len(pts) >= 2:
+            x, y = np.array(pts).T
+            fits[mname] = float(np.polyfit(x, y, 1)[0])
+    dev = {str(c): abs(rows["triad_%d" % c]["lnz"] - rows["atrg_%d" % c]["lnz"]) / abs(rows["atrg_%d" % c]["lnz"])
+           for c in chis}
+    doc = {"config": "4D Ising, beta=0.1497 h=0, r=7, q=2, seed 2, precision %s" % args.precision,
+           "command": "python bench.py --methods-run --methods-chis %s --steps %d --methods-steps %d --precision %s"
+                      % (args.methods_chis, args.steps, args.methods_steps, args.precision),
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+           "time_exponent": fits, "triad_vs_atrg_rel_lnz": dev, "runs": rows}
+    os.makedirs(os.path.dirname(METHODS_FILE), exist_ok=True)
+    with open(METHODS_FILE, "w") as f:
+        json.dump(doc, f, indent=1)
+    print(json.dumps({"time_exponent": fits, "triad_vs_atrg_rel_lnz": dev}), flush=True)
+
+
+C5_FILE = os.path.join(ROOT, "profiles", "c5_grad_chi32.json")
+
+
+def run_c5(args):
+    """The derivative configuration: chi = 32, r = 2, q = 2, 32 steps, beta = 0.1497,
+    h in {0, 1e-3}, seed 4.  The forward-mode derivatives of tatrg_grad (dlnZ/dbeta,
+    dlnZ/dh, d2lnZ/dbeta2 per site) against central differences of the GPU's own FP64
+    ln Z / V: step 1e-5 for the first derivatives, step 1e-4 for the second.  Writes
+    profiles/c5_grad_chi32.json; prints one JSON line."""
+    import torch
+    import paper_2412_14104_gb300 as tg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    chi, r, steps, seed, beta = 32, 2, 32, 4, 0.1497
+
+    def lnz(b, h):
+        return tg.Context(chi, r, Q, seed=seed, stream=stream).init_ising(b, h, 4).rg_step(steps).lnZ()
+
+    out = {}
+    for h in (0.0, 1e-3):
+        t0 = time.perf_counter()
+        ctx = tg.Context(chi, r, Q, seed=seed, stream=stream).init_ising(beta, h, 4).rg_step(steps)
+        z0 = ctx.lnZ()
+        gb, gh, c2 = ctx.grad(second=True)
+        t_grad = time.perf_counter() - t0
+        e1, e2 = 1e-5, 1e-4
+        zb = {d: lnz(beta + d, h) for d in (-e2, -e1, e1, e2)}
+        fd_b = (zb[e1] - zb[-e1]) / (2 * e1)
+        fd_c = (zb[e2] - 2 * z0 + zb[-e2]) / (e2 * e2)
+        row = {"lnz": z0, "dlnz_dbeta": gb, "fd_dlnz_dbeta": fd_b,
+               "rel_dbeta": abs(gb - fd_b) / abs(fd_b),
+               "d2lnz_dbeta2": c2, "fd_d2lnz_dbeta2": fd_c, "rel_d2beta": abs(c2 - fd_c) / abs(fd_c),
+               "grad_s": t_grad}
+        if h != 0.0:
+            fd_h = (lnz(beta, h + e1) - lnz(beta, h - e1)) / (2 * e1)
+            row.update({"dlnz_dh": gh, "fd_dlnz_dh": fd_h, "rel_dh": abs(gh - fd_h) / abs(fd_h)})
+        out["h=%g" % h] = row
+        print(json.dumps({"h": h, **row}), flush=True)
+    doc = {"config": "chi=32 r=2 q=2, 32 steps, beta=0.1497, seed 4, d=4, FP64",
+           "command": "python bench.py --c5-run",
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "results": out}
+    os.makedirs(os.path.dirname(C5_FILE), exist_ok=True)
+    with open(C5_FILE, "w") as f:
+        json.dump(doc, f, indent=1)
+
+
+C4_FILE = os.path.join(ROOT, "profiles", "c4_sweep_chi32.json")
+
+
+def run_c4(args):
+    """The temperature-sweep configuration: 64 temperatures uniformly spaced in
+    beta in [0.145, 0.155], h = 0, chi = 32, r = 2, q = 2, 32 steps each, split precision
+    (3xTF32), seed 3.  Times tatrg_sweep_observables (the runs on concurrent workers) against
+    the same 64 runs one after another, and reads the order parameter X^(m) of every run to
+    locate the transition (X crosses 1.5 between the disordered value 1 and the ordered
+    value 2).  Writes profiles/c4_sweep_chi32.json; prints one JSON line."""
+    import numpy as np
+    import torch
+    import paper_2412_14104_gb300 as tg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    betas = 0.145 + np.arange(64) * (0.01 / 63)
+    chi, r, steps, seed = 32, 2, 32, 3
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}[args.precision]
+    ctx = tg.Context(chi, r, Q, seed=seed, precision=prec, sweep_workers=args.sweep_workers, stream=stream)
+    ctx.sweep_observables(betas[:2], 0.0, 4, steps)  # first-use setup (tuning of the shapes)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    z, x = ctx.sweep_observables(betas, 0.0, 4, steps)
+    torch.cuda.synchronize()
+    t_sweep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    z1 = []
+    for i, b in enumerate(betas[:args.c4_serial]):
+        c = tg.Context(chi, r, Q, seed=seed, precision=prec, stream=stream)
+        c.init_ising(float(b), 0.0, 4).rg_step(steps)
+        z1.append(c.lnZ())
+        c.close()
+    torch.cuda.synchronize()
+    t_serial = (time.perf_counter() - t0) * len(betas) / max(1, args.c4_serial)
+    cross = None
+    for i in range(len(betas) - 1):
+        if (x[i] - 1.5) * (x[i + 1] - 1.5) <= 0 and x[i] != x[i + 1]:
+            cross = float(betas[i] + (1.5 - x[i]) * (betas[i + 1] - betas[i]) / (x[i + 1] - x[i]))
+            break
+    doc = {"config": "64 beta in [0.145, 0.155], h=0, chi=32 r=2 q=2, 32 steps, %s, seed 3, %d workers"
+                     % (args.precision, args.sweep_workers),
+           "command": "python bench.py --c4-run --sweep-workers %d --c4-serial %d --precision %s"
+                      % (args.sweep_workers, args.c4_serial, args.precision),
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+           "sweep_s": t_sweep, "serial_s_for_64": t_serial,
+           "serial_note": "the first %d runs one after another, scaled to 64" % args.c4_serial,
+           "runs_per_s_sweep": len(betas) / t_sweep, "runs_per_s_serial": len(betas) / t_serial,
+           "rg_steps_per_s_sweep": len(betas) * steps / t_sweep,
+           "serial_matches_sweep": [abs(a - b) / abs(b) for a, b in zip(z1, z[:len(z1)])],
+           "beta_c_estimate": cross, "betas": betas.tolist(), "lnz": z.tolist(), "X": x.tolist()}
+    os.makedirs(os.path.dirname(C4_FILE), exist_ok=True)
+    with open(C4_FILE, "w") as f:
+        json.dump(doc, f, indent=1)
+    print(json.dumps({k: doc[k] for k in ("config", "sweep_s", "serial_s_for_64", "runs_per_s_sweep",
+                                          "runs_per_s_serial", "beta_c_estimate")}), flush=True)
+
+
+D3_FILE = os.path.join(ROOT, "profiles", "d3_runs.json")
+
+
+def run_d3(args):
+    """3D Ising production runs (the MDTRG comparison system of Sec. 1): Triad-ATRG at the 3D
+    critical coupling beta = 0.2216544, h = 0, r = 2, q = 2, 30 steps, chi in --d3-chis,
+    split precision from step 13; ln Z / V and the steady-state step time per chi.  Writes
+    profiles/d3_runs.json."""
+    import torch
+    import paper_2412_14104_gb300 as tg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}[args.precision]
+    rows = {}
+    for chi in [int(c) for c in args.d3_chis.split(",")]:
+        ctx = tg.Context(chi, 2, Q, seed=6, precision=prec, split_from_step=13, stream=stream)
+        ctx.init_ising(0.2216544, 0.0, 3)
+        ms = []
+        for k in range(30):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.rg_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        rows[str(chi)] = {"lnz": ctx.lnZ(), "ms_last_steps": sum(ms[-5:]) / 5, "run_s": sum(ms) / 1e3}
+        ctx.close()
+        print("d3 chi=%d: %s" % (chi, rows[str(chi)]), flush=True)
+    doc = {"config": "3D Ising beta=0.2216544 h=0, r=2 q=2, 30 steps, %s from step 13, seed 6" % args.precision,
+           "command": "python bench.py --d3-run --d3-chis %s --precision %s" % (args.d3_chis, args.precision),
+           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "runs": rows}
+    os.makedirs(os.path.dirname(D3_FILE), exist_ok=True)
+    with open(D3_FILE, "w") as f:
+        json.dump(doc, f, indent=1)
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -354,7 +554,7 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "fp64": tg.FP64}[args.precision]
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}[args.precision]
     seed = SEED + 1000 * rank
     chi, r = args.chi, args.r
     ctx = tg.Context(chi, r, Q, seed=seed, precision=prec, profile=1, stream=stream)
@@ -399,7 +599,7 @@ def run_ours(args, world, rank, local):
     for p_, a in zip(pins, (A, s, B)):
         p_.numpy()[...] = a
     hA, hs, hB = (p_.numpy() for p_ in pins)
-    e2e_steps = max(1, min(2, args.steps))
+    e2e_steps = max(1, min(5, args.steps))
     k0 = ctx.step_info().step
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -420,8 +620,9 @@ def run_ours(args, world, rank, local):
     else:
         peak, note = bf16, "%s bf16 sustained" % src
     # achieved: algorithmic flops (2 M N K per contraction) over the kernel's device time;
-    # the split form issues 3 tensor-core products per algorithmic one
+    # the split forms issue 3 (6 for bf16x6) tensor-core products per algorithmic one
     achieved = tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
+    nprod = 6.0 if prec == tg.BF16X6 else 3.0
     traffic = None  # DRAM bytes per launch from the committed ncu capture of this workload
     prof = os.path.join(ROOT, "profiles", "tc_gemm_chi48_traffic.json")
     if os.path.exists(prof) and (chi, r) == (CHI, R) and prec == tg.TF32X3:
@@ -469,9 +670,9 @@ def run_ours(args, world, rank, local):
                      "avg_launch_ms": tc_ms / max(tc_launches, 1),
                      "flops_per_launch": tc_flops / max(tc_launches, 1),
                      "hardware_products": {
-                         "achieved": 3.0 * achieved if achieved else None,
-                         "frac": (3.0 * achieved / peak) if achieved else None,
-                         "note": "3 tensor-core products per algorithmic product (hi*hi, hi*lo, lo*hi)"}},
+                         "achieved": nprod * achieved if achieved else None,
+                         "frac": (nprod * achieved / peak) if achieved else None,
+                         "note": "%d tensor-core products per algorithmic product" % nprod}},
         "e2e": {"value": e2e_steps * world / e2e_s, "unit": "RG steps/s",
                 "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
         "gpu_launches": launches,
@@ -486,6 +687,20 @@ def run_ours(args, world, rank, local):
                                          note="stored whole-run measurement (not re-run by this "
                                               "command); the FP64 GPU step is checked against the "
                                               "oracle by the chi = 48 teacher-forced step test")
+    stored = {}
+    for name, path, keys in (
+            ("c4_sweep", C4_FILE, ("config", "when", "command", "runs_per_s_sweep", "runs_per_s_serial",
+                                   "rg_steps_per_s_sweep", "beta_c_estimate")),
+            ("c5_grad", C5_FILE, ("config", "when", "command", "results")),
+            ("methods", METHODS_FILE, ("config", "when", "command", "time_exponent", "triad_vs_atrg_rel_lnz")),
+            ("d3", D3_FILE, ("config", "when", "command", "runs"))):
+        if os.path.exists(path):
+            with open(path) as f:
+                doc = json.load(f)
+            stored[name] = {k: doc.get(k) for k in keys}
+    if stored:
+        line["stored_runs"] = dict(stored, note="whole-run measurements of the other configurations, "
+                                                "written by the commands named in each (not re-run here)")
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_record(10.0)
     print(json.dumps(line), flush=True)
@@ -497,7 +712,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "bf16x6", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-delta-f", action="store_true")
@@ -509,7 +724,31 @@ def main():
     ap.add_argument("--c3-run", action="store_true",
                     help="run the 40-step chi = 48 configuration in the forms of --c3-forms")
     ap.add_argument("--c3-forms", default="fp64,tf32x3@1,bf16x3@1,tf32x3@5,bf16x3@5,tf32x3@9,bf16x3@9,tf32x3@13,bf16x3@13")
+    ap.add_argument("--methods-run", action="store_true",
+                    help="Triad-ATRG against ATRG (r = 7): step time and ln Z / V per chi")
+    ap.add_argument("--methods-chis", default="8,12,16,20,24")
+    ap.add_argument("--methods-steps", type=int, default=24)
+    ap.add_argument("--c5-run", action="store_true",
+                    help="derivatives at chi = 32, 32 steps against central differences")
+    ap.add_argument("--c4-run", action="store_true", help="the 64-temperature sweep at chi = 32")
+    ap.add_argument("--sweep-workers", type=int, default=8)
+    ap.add_argument("--c4-serial", type=int, default=16,
+                    help="runs timed one after another for the serial comparison (scaled to 64)")
+    ap.add_argument("--d3-run", action="store_true", help="3D Ising runs over --d3-chis")
+    ap.add_argument("--d3-chis", default="16,24,32,48,64")
     args = ap.parse_args()
+    if args.c4_run:
+        run_c4(args)
+        return
+    if args.d3_run:
+        run_d3(args)
+        return
+    if args.c5_run:
+        run_c5(args)
+        return
+    if args.methods_run:
+        run_methods(args)
+        return
     if args.c3_run:
         run_c3(args)
         return

@@ -49,7 +49,10 @@ typedef enum { TATRG_ATRG = 0, TATRG_TRIAD = 1 } tatrg_method;
 typedef enum {
   TATRG_FP64 = 0,   /* float64 CUDA-core GEMMs */
   TATRG_TF32X3 = 1, /* tcgen05 kind::tf32, operands split hi+lo, 3 products, FP32 accumulate */
-  TATRG_BF16X3 = 2  /* tcgen05 kind::f16 with bf16 hi+lo split, 3 products, FP32 accumulate */
+  TATRG_BF16X3 = 2, /* tcgen05 kind::f16 with bf16 hi+lo split, 3 products, FP32 accumulate */
+  TATRG_BF16X6 = 3  /* tcgen05 kind::f16 with bf16 hi+mid+lo split (the 24 bits of the float
+                       nearest to each operand), the 6 products down to 2^-16 of hi*hi,
+                       FP32 accumulate: the tensor time of TATRG_TF32X3 at float accuracy */
 } tatrg_precision;
 
 typedef struct {
@@ -212,7 +215,7 @@ tatrg_status tatrg_contract(const tatrg_contraction* c, int precision, const dou
  * element B[k, n] is sketch element number sum_i k_i k_sB[i] + sum_i n_i n_sB[i]), generated
  * while the tensor-core operand is packed and never stored: the random test matrix of the
  * randomized SVD (Halko et al. Alg. 4.4, used for the bond swap of Eq. 1, Table 1) drawn in
- * the contraction's operand producer.  Only for the split precisions (precision 1 or 2,
+ * the contraction's operand producer.  Only for the split precisions (precision 1, 2 or 3,
  * where Box-Muller runs in float arithmetic: the values equal tatrg_gaussian's rounded to
  * float) and contractions large enough for the tensor cores (EINVAL otherwise).  The
  * result equals tatrg_contract on that sketch rounded to float, stored.  Synchronises. */

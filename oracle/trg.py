@@ -47,7 +47,7 @@ TAU = 1e-10  # relative gap (s_i - s_i+1) / s_i below which values form one mult
 class Params:
     """chi=None and r=None select the untruncated ("chi = infinity") mode."""
 
-    def __init__(self, chi, r, q=2, method="triad", seed=0, replica=0):
+    def __init__(self, chi, r, q=2, method="triad", seed=0, replica=0, split_tau=None, split_from_step=1):
         if method not in ("triad", "atrg"):
             raise ValueError(method)
         self.chi = chi
@@ -56,6 +56,15 @@ class Params:
         self.method = method
         self.seed = int(seed)
         self.replica = int(replica)
+        # multiplet gap used from split_from_step on (the library's split-precision steps
+        # use 1e-6); None keeps TAU everywhere
+        self.split_tau = split_tau
+        self.split_from_step = int(split_from_step)
+
+    def tau(self, step):
+        if self.split_tau is not None and step >= self.split_from_step:
+            return self.split_tau
+        return TAU
 
     def cap(self):
         return None if self.chi is None else int(self.chi)
@@ -161,7 +170,7 @@ def bond_swap(A, s, B, p, step, cnt=None, info=None):
                              p.replica)
         U, S, V = rla.rsvd(op, ell, p.q, om)
         exact = False
-    Dg = rla.multiplet_cut(S, rla.keep_count(S, 1e-14, p.cap()), TAU)
+    Dg = rla.multiplet_cut(S, rla.keep_count(S, 1e-14, p.cap()), p.tau(step))
     X, sgn = rla.fix_sign(U[:, :Dg])
     Y = V[:, :Dg] * sgn[None, :]
     if info is not None:
@@ -308,11 +317,11 @@ def squeezers(rho_l, rho_r, p, step, cnt=None, info=None):
         RR = _factor(rho_r[nu - 1], p, step, philox.KIND_SQ_RIGHT + nu - 1, cnt)
         C = RL @ RR.T
         U, S, V = rla.svd_desc(C)
-        k = rla.multiplet_cut(S, rla.keep_count(S, 1e-12, p.cap()), TAU)
+        k = rla.multiplet_cut(S, rla.keep_count(S, 1e-12, p.cap()), p.tau(step))
         isq = 1.0 / np.sqrt(S[:k])
         M = (RR.T @ V[:, :k]) * isq[None, :]
         N = (U[:, :k] * isq[None, :]).T @ RL
-        M, O = rla.canonical_basis(M, S[:k], TAU)
+        M, O = rla.canonical_basis(M, S[:k], p.tau(step))
         N = O.T @ N
         Dn = int(round(math.sqrt(M.shape[0])))
         Ms.append(M.reshape(Dn, Dn, k))
@@ -388,7 +397,7 @@ def contract(E, F, G, H, I, J, K, L, Ms, Ns, g, cnt=None):
     return phi, psi
 
 
-def resplit(phi, psi, p, cnt=None, info=None):
+def resplit(phi, psi, p, cnt=None, info=None, step=0):
     """T' = Phi Psi^T = A' s' B' through two thin QRs and a small SVD; normalise; rotate."""
     d = phi.ndim - 1
     Dg = phi.shape[-1]
@@ -410,7 +419,7 @@ def resplit(phi, psi, p, cnt=None, info=None):
     rot = tuple(range(1, d)) + (0, d)
     An = np.ascontiguousarray(np.transpose(An, rot))
     Bn = np.ascontiguousarray(np.transpose(Bn, rot))
-    am, O = rla.canonical_basis(An.reshape(-1, Da), s, TAU)
+    am, O = rla.canonical_basis(An.reshape(-1, Da), s, p.tau(step))
     bm = Bn.reshape(-1, Da) @ O
     if info is not None:
         info["s"] = s.copy()
@@ -428,7 +437,7 @@ def rg_step(A, s, B, p, step, cnt=None, info=None):
     rho_l, rho_r = squeezer_grams(E, F, G, H, I, J, K, L, g, cnt)
     Ms, Ns = squeezers(rho_l, rho_r, p, step, cnt, info)
     phi, psi = contract(E, F, G, H, I, J, K, L, Ms, Ns, g, cnt)
-    return resplit(phi, psi, p, cnt, info)
+    return resplit(phi, psi, p, cnt, info, step)
 
 
 def trace(A, s, B):

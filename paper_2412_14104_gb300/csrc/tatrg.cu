@@ -1409,7 +1409,7 @@ tatrg_status tatrg_create(const tatrg_params* params, void* cuda_stream, tatrg_c
                 "tatrg_create: need chi >= 1, r >= 1, q >= 0");
     TATRG_CHECK(params->method == TATRG_ATRG || params->method == TATRG_TRIAD, TATRG_EINVAL,
                 "tatrg_create: unknown method");
-    TATRG_CHECK(params->precision >= TATRG_FP64 && params->precision <= TATRG_BF16X3, TATRG_EINVAL,
+    TATRG_CHECK(params->precision >= TATRG_FP64 && params->precision <= TATRG_BF16X6, TATRG_EINVAL,
                 "tatrg_create: unknown precision");
     // The step's buffers come from the device's stream-ordered pool; keep freed blocks in
     // the pool across synchronisations instead of returning them to the driver each time.
@@ -1684,8 +1684,8 @@ tatrg_status tatrg_contract_sketch(const tatrg_contraction* c, int precision, co
                                    void* stream) {
   return guard(nullptr, [&] {
     TATRG_CHECK(c && A && C, TATRG_EINVAL, "tatrg_contract_sketch: null argument");
-    TATRG_CHECK(precision == 1 || precision == 2, TATRG_EINVAL,
-                "tatrg_contract_sketch: needs a split precision (1 or 2)");
+    TATRG_CHECK(precision >= 1 && precision <= 3, TATRG_EINVAL,
+                "tatrg_contract_sketch: needs a split precision (1, 2 or 3)");
     const GemmDesc g = desc_of(c);
     Engine e(static_cast<cudaStream_t>(stream));
     e.prec = precision;
@@ -1701,7 +1701,7 @@ tatrg_status tatrg_contract(const tatrg_contraction* c, int precision, const dou
                             double* C, void* stream) {
   return guard(nullptr, [&] {
     TATRG_CHECK(c && A && B && C, TATRG_EINVAL, "tatrg_contract: null argument");
-    TATRG_CHECK(precision >= 0 && precision <= 2, TATRG_EINVAL, "tatrg_contract: bad precision");
+    TATRG_CHECK(precision >= 0 && precision <= 3, TATRG_EINVAL, "tatrg_contract: bad precision");
     GemmDesc g;
     g.m = modes({{c->m_ext[0], c->m_sA[0], c->m_sC[0]}, {c->m_ext[1], c->m_sA[1], c->m_sC[1]},
                  {c->m_ext[2], c->m_sA[2], c->m_sC[2]}, {c->m_ext[3], c->m_sA[3], c->m_sC[3]}});
@@ -1728,7 +1728,7 @@ tatrg_status tatrg_orth(int precision, int64_t m, int64_t n, const double* Y, do
                         int* k, void* stream) {
   return guard(nullptr, [&] {
     TATRG_CHECK(Y && Q && R && k && m >= n && n >= 1 && n <= 1024, TATRG_EINVAL, "tatrg_orth: bad argument");
-    TATRG_CHECK(precision >= 0 && precision <= 2, TATRG_EINVAL, "tatrg_orth: bad precision");
+    TATRG_CHECK(precision >= 0 && precision <= 3, TATRG_EINVAL, "tatrg_orth: bad precision");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Engine e(s);
     e.prec = precision;

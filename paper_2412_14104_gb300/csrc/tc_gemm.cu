@@ -18,6 +18,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <tuple>
+
 #include "kernels.cuh"
 #include "philox.cuh"
 
@@ -350,18 +352,34 @@ __device__ __forceinline__ bool epilogue_all(bool p) {
 // CTA's warp 1 tells it, through a barrier in the first CTA's shared memory, when each of
 // its stages has landed, and the second CTA's epilogue warps arrive on the first CTA's
 // accumulator-empty barriers.  Per SM this halves the B operand traffic of each MMA.
-template <int PREC, int KC, int STAGES, int NBUF, bool PAIR>
+// NS slices per operand (2: hi, lo; 3: hi, mid, lo); the products kept are those whose
+// slice indices (0 = hi) sum to at most NS - 1, issued smallest first
+//   NS = 2: lo*hi, hi*lo, hi*hi;  NS = 3: lo*hi, hi*lo, mid*mid, mid*hi, hi*mid, hi*hi
+template <int NS>
+struct Products {
+  static constexpr int n = NS == 2 ? 3 : 6;
+  __device__ __forceinline__ static constexpr int a(int t) {
+    return NS == 2 ? (t == 0 ? 1 : 0) : (t == 0 ? 2 : t == 1 ? 0 : t == 2 ? 1 : t == 3 ? 1 : 0);
+  }
+  __device__ __forceinline__ static constexpr int b(int t) {
+    return NS == 2 ? (t == 1 ? 1 : 0) : (t == 0 ? 0 : t == 1 ? 2 : t == 2 ? 1 : t == 3 ? 0 : t == 4 ? 1 : 0);
+  }
+};
+
+struct TcMaps {
+  CUtensorMap a[3], b[3];  // slice panels of A and B (the first NS are used)
+};
+
+template <int PREC, int NS, int KC, int STAGES, int NBUF, bool PAIR>
 __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's register file
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
-                   const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
-                   TcArgs g) {
+    tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
   constexpr int CG = PAIR ? 2 : 1;
   constexpr int BN = TC_BN;
   constexpr int TILE_M = TC_BM * CG;        // output rows per tile (per pair)
   constexpr int B_ROWS = BN / CG;           // rows of B (output columns) per CTA
   constexpr int A_TILE = TC_BM * KSLICE;    // bytes
   constexpr int B_TILE = B_ROWS * KSLICE;
-  constexpr int STAGE = 2 * A_TILE + 2 * B_TILE;
+  constexpr int STAGE = NS * (A_TILE + B_TILE);
   constexpr int KELEM = PREC == 1 ? KSLICE / 4 : KSLICE / 2;  // K elements per stage
   constexpr int TMEM_COLS = NBUF * BN + 2 * BN;  // chunk buffers, running hi, running lo
   static_assert(TMEM_COLS == 512, "the tensor memory holds exactly 512 columns");
@@ -415,10 +433,11 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
           mbar_expect_tx(&full_bar[s], STAGE);
           const int kx = (w.kb0 + i) * KELEM;
           const int ya = int(w.m0) + int(rank) * TC_BM, yb = int(w.n0) + int(rank) * B_ROWS;
-          tma_load_2d(st, &ta_hi, &full_bar[s], kx, ya);
-          tma_load_2d(st + A_TILE, &ta_lo, &full_bar[s], kx, ya);
-          tma_load_2d(st + 2 * A_TILE, &tb_hi, &full_bar[s], kx, yb);
-          tma_load_2d(st + 2 * A_TILE + B_TILE, &tb_lo, &full_bar[s], kx, yb);
+#pragma unroll
+          for (int p = 0; p < NS; ++p) {
+            tma_load_2d(st + p * A_TILE, &maps.a[p], &full_bar[s], kx, ya);
+            tma_load_2d(st + NS * A_TILE + p * B_TILE, &maps.b[p], &full_bar[s], kx, yb);
+          }
         }
       }
       // drain: the last loads issued into each stage must have landed before the CTA exits
@@ -446,14 +465,15 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
             if (PAIR && !mbar_wait<true>(&peer_full[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
             tc_fence_after();
             const uint32_t base = smem_u32(smem + s * STAGE);
-            const uint64_t ahi = sdesc_sw(base), alo = sdesc_sw(base + A_TILE);
-            const uint64_t bhi = sdesc_sw(base + 2 * A_TILE), blo = sdesc_sw(base + 2 * A_TILE + B_TILE);
 #pragma unroll
             for (int kk = 0; kk < KSLICE / 32; ++kk) {  // 32 bytes of K per instruction
               const uint64_t off = uint64_t(kk * 2);
-              mma<PREC, CG>(acc, alo + off, bhi + off, id, (i > c * KC || kk > 0) ? 1u : 0u);
-              mma<PREC, CG>(acc, ahi + off, blo + off, id, 1u);
-              mma<PREC, CG>(acc, ahi + off, bhi + off, id, 1u);
+#pragma unroll
+              for (int t = 0; t < Products<NS>::n; ++t) {
+                const uint64_t ad = sdesc_sw(base + Products<NS>::a(t) * A_TILE) + off;
+                const uint64_t bd = sdesc_sw(base + NS * A_TILE + Products<NS>::b(t) * B_TILE) + off;
+                mma<PREC, CG>(acc, ad, bd, id, (i > c * KC || kk > 0 || t > 0) ? 1u : 0u);
+              }
             }
             mma_commit<CG>(&empty_bar[s]);
           }
@@ -647,21 +667,28 @@ __device__ __forceinline__ float tf32_rna(float x) {
 // written from it with the lanes along K.
 constexpr int PK_R = 32, PK_K = 128;
 
-template <int PREC>
-__device__ __forceinline__ void pack_store(void* hi, void* lo, int64_t o, double x) {
+// destinations of the NS slices of a packed operand
+struct PackDst {
+  void* p[3];
+};
+
+template <int PREC, int NS>
+__device__ __forceinline__ void pack_store(const PackDst& dst, int64_t o, double x) {
+  // split the float nearest to x (its 24 bits hold more than hi + lo keep; hi + mid + lo of
+  // bf16 keep all of them); each residual is exact in float
+  const float f = d2f_bits(x);
   if (PREC == 1) {
-    // split the float nearest to x (its 24 bits hold more than hi + lo keep)
-    const float f = d2f_bits(x);
     const float h = tf32_rna(f);
     const float l = tf32_rna(__fsub_rn(f, h));
-    reinterpret_cast<float*>(hi)[o] = h;
-    reinterpret_cast<float*>(lo)[o] = l;
+    reinterpret_cast<float*>(dst.p[0])[o] = h;
+    reinterpret_cast<float*>(dst.p[1])[o] = l;
   } else {
-    const float f = d2f_bits(x);
     const __nv_bfloat16 h = __float2bfloat16_rn(f);
-    const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(f, __bfloat162float(h)));
-    reinterpret_cast<__nv_bfloat16*>(hi)[o] = h;
-    reinterpret_cast<__nv_bfloat16*>(lo)[o] = l;
+    const float r = __fsub_rn(f, __bfloat162float(h));
+    const __nv_bfloat16 m = __float2bfloat16_rn(r);
+    reinterpret_cast<__nv_bfloat16*>(dst.p[0])[o] = h;
+    reinterpret_cast<__nv_bfloat16*>(dst.p[1])[o] = m;
+    if (NS == 3) reinterpret_cast<__nv_bfloat16*>(dst.p[2])[o] = __float2bfloat16_rn(__fsub_rn(r, __bfloat162float(m)));
   }
 }
 
@@ -678,11 +705,11 @@ __device__ __forceinline__ double operand_at(const double* __restrict__ src, con
   return __ldg(src + off);
 }
 
-template <int PREC, bool GEN>
+template <int PREC, int NS, bool GEN>
 __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ src, DevModes rm,
                                                    DevModes km, int64_t R, int64_t K, int64_t Kp,
-                                                   int64_t ktiles, int64_t ntiles, void* hi,
-                                                   void* lo, int r_contig, GaussSrc gs) {
+                                                   int64_t ktiles, int64_t ntiles, PackDst dst,
+                                                   int r_contig, GaussSrc gs) {
   __shared__ int64_t roff[PK_R], koff[PK_K];
   __shared__ double tile[PK_R][PK_K + 1];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;  // 8 warps
@@ -726,8 +753,8 @@ __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ sr
               if (r + 1 < R) v1 = operand_at<PREC, true>(src, gs, o1);
             }
           }
-          pack_store<PREC>(hi, lo, r * Kp + k, v0);
-          pack_store<PREC>(hi, lo, (r + 1) * Kp + k, v1);
+          pack_store<PREC, NS>(dst, r * Kp + k, v0);
+          pack_store<PREC, NS>(dst, (r + 1) * Kp + k, v1);
         }
       }
     } else if (!r_contig) {
@@ -745,7 +772,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ sr
 #pragma unroll
         for (int j = 0; j < PK_K / 32; ++j) {
           const int64_t k = k0 + lane + 32 * j;
-          if (k < Kp) pack_store<PREC>(hi, lo, r * Kp + k, v[j]);
+          if (k < Kp) pack_store<PREC, NS>(dst, r * Kp + k, v[j]);
         }
       }
     } else {
@@ -763,7 +790,7 @@ __global__ void __launch_bounds__(256) pack_kernel(const double* __restrict__ sr
 #pragma unroll
         for (int j = 0; j < PK_K / 32; ++j) {
           const int64_t k = k0 + lane + 32 * j;
-          if (k < Kp) pack_store<PREC>(hi, lo, (r0 + rr) * Kp + k, tile[rr][lane + 32 * j]);
+          if (k < Kp) pack_store<PREC, NS>(dst, (r0 + rr) * Kp + k, tile[rr][lane + 32 * j]);
         }
       }
     }
@@ -814,12 +841,12 @@ CUtensorMap make_map(void* base, int64_t rows, int64_t kp, int esize, int box_ro
   return m;
 }
 
-// Shared-memory ring of the kernel: stages of A (hi, lo) and B (hi, lo) slices.
-template <bool PAIR>
-constexpr int stage_bytes() { return 2 * TC_BM * KSLICE + 2 * (PAIR ? TC_BN / 2 : TC_BN) * KSLICE; }
+// Shared-memory ring of the kernel: stages of the NS slices of A and of B.
+template <int NS, bool PAIR>
+constexpr int stage_bytes() { return NS * (TC_BM * KSLICE + (PAIR ? TC_BN / 2 : TC_BN) * KSLICE); }
 
 // Largest number of CTAs (of pairs: clusters) that are resident at once, per device.
-template <int PREC, bool PAIR>
+template <int PREC, int NS, bool PAIR>
 int resident_units(const void* kfn, int smem) {
   static std::mutex mu;
   static std::map<int, int> cache;
@@ -854,20 +881,20 @@ int resident_units(const void* kfn, int smem) {
   return n;
 }
 
-template <int PREC, bool PAIR>
-void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& bhi,
-            const CUtensorMap& blo, const TcArgs& a, int64_t units, cudaStream_t s) {
-  constexpr int STAGE = stage_bytes<PAIR>();
+template <int PREC, int NS, bool PAIR>
+void launch(const TcMaps& maps, const TcArgs& a, int64_t units, cudaStream_t s) {
+  constexpr int STAGE = stage_bytes<NS, PAIR>();
   constexpr int STAGES = SMEM_BUDGET / STAGE;
+  static_assert(STAGES >= 2, "the ring needs two stages");
   constexpr int KC = TATRG_CHAIN_K / (PREC == 1 ? KSLICE / 4 : KSLICE / 2);  // stages per FP32 chain
   static_assert(KC >= 1, "an FP32 chain spans at least one stage");
   constexpr int SMEM = STAGES * STAGE + 1024;
-  auto k = tc_gemm_kernel<PREC, KC, STAGES, 2, PAIR>;
-  const int resident = resident_units<PREC, PAIR>(reinterpret_cast<const void*>(k), SMEM);
+  auto k = tc_gemm_kernel<PREC, NS, KC, STAGES, 2, PAIR>;
+  const int resident = resident_units<PREC, NS, PAIR>(reinterpret_cast<const void*>(k), SMEM);
   // persistent: every CTA (pair) walks units b, b + grid, ...; no more CTAs than are resident
   const unsigned n = unsigned(std::min<int64_t>(units, resident));
   if (!PAIR) {
-    k<<<n, TC_THREADS, SMEM, s>>>(ahi, alo, bhi, blo, a);
+    k<<<n, TC_THREADS, SMEM, s>>>(maps, a);
   } else {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -881,7 +908,7 @@ void launch(const CUtensorMap& ahi, const CUtensorMap& alo, const CUtensorMap& b
     cfg.stream = s;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    TATRG_CUDA(cudaLaunchKernelEx(&cfg, k, ahi, alo, bhi, blo, a));
+    TATRG_CUDA(cudaLaunchKernelEx(&cfg, k, maps, a));
   }
   TATRG_CUDA(cudaGetLastError());
 }
@@ -925,9 +952,84 @@ int tc_error_flag(bool reset) {
   return h;
 }
 
+namespace {
+// Autotuner of the launch configuration: the first time a large contraction of a given
+// shape is seen on a device (and its output is overwritten, beta = 0), every candidate --
+// single CTAs or CTA pairs, the split-K heuristic's factor, half and twice it -- runs once
+// on the real operands, timed with CUDA events; the fastest is kept for that shape.  Each
+// candidate computes the whole result, so the output of the last one stands.  Smaller
+// contractions, and shapes not yet tuned whose output is accumulated into, take the
+// heuristic with pairs where allowed.  TATRG_AUTOTUNE=0 turns tuning off.
+struct TcChoice {
+  bool pair = false;
+  int split = 1;
+};
+
+constexpr double kTuneFlops = 2e11;  // contractions below this are not tuned
+
+template <class Heur, class Run>
+TcChoice tuned_choice(int prec, int64_t M, int64_t N, int64_t K, int n_contig, bool pair_ok, bool may_tune,
+                      Heur& heuristic, Run& run, cudaStream_t s) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int64_t, int64_t, int64_t, int, bool>, TcChoice> cache;
+  static const bool on = []() {
+    const char* e = getenv("TATRG_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  int dev = 0;
+  TATRG_CUDA(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, prec, M, N, K, n_contig, pair_ok);
+  {
+    std::lock_guard<std::mutex> l(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  TcChoice def;
+  def.pair = pair_ok;
+  def.split = heuristic(pair_ok);
+  if (!on || !may_tune || 2.0 * double(M) * double(N) * double(K) < kTuneFlops) return def;
+  std::vector<TcChoice> cand;
+  for (int p = 0; p <= (pair_ok ? 1 : 0); ++p) {
+    const int h = heuristic(p == 1);
+    for (int sp : {h, std::max(1, h / 2), std::min(512, 2 * h)}) {
+      bool dup = false;
+      for (const auto& c : cand) dup = dup || (c.pair == (p == 1) && c.split == sp);
+      if (!dup) cand.push_back(TcChoice{p == 1, sp});
+    }
+  }
+  cudaEvent_t ev[2];
+  TATRG_CUDA(cudaEventCreate(&ev[0]));
+  TATRG_CUDA(cudaEventCreate(&ev[1]));
+  TcChoice best = def;
+  float best_ms = 1e30f;
+  for (const auto& c : cand) {
+    TATRG_CUDA(cudaEventRecord(ev[0], s));
+    run(c.pair, c.split);
+    TATRG_CUDA(cudaEventRecord(ev[1], s));
+    TATRG_CUDA(cudaEventSynchronize(ev[1]));
+    float ms = 0.f;
+    TATRG_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  static const bool log = []() {
+    const char* e = getenv("TATRG_AUTOTUNE_LOG");
+    return e && e[0] == '1';
+  }();
+  if (log)
+    fprintf(stderr, "tatrg autotune: M=%lld N=%lld K=%lld prec=%d -> %s split %d (%.3f ms of %zu candidates)\n",
+            (long long)M, (long long)N, (long long)K, prec, best.pair ? "pair" : "single", best.split, best_ms,
+            cand.size());
+  std::lock_guard<std::mutex> l(mu);
+  cache[key] = best;
+  return best;
+}
+}  // namespace
+
 void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int prec,
              cudaStream_t s, Stats* st, const GaussSrc* gen_b) {
-  TATRG_CHECK(prec == 1 || prec == 2, TATRG_EINVAL, "gemm_tc: precision must be TF32X3 or BF16X3");
+  TATRG_CHECK(prec >= 1 && prec <= 3, TATRG_EINVAL, "gemm_tc: precision must be TF32X3, BF16X3 or BF16X6");
   TATRG_CHECK(tc_available(), TATRG_ENOTIMPL, "gemm_tc: tcgen05 path needs an sm_103 GPU");
   const int64_t M = d.m.total(), N = d.n.total(), K = d.k.total();
   if (M == 0 || N == 0) return;
@@ -939,76 +1041,72 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     check_gemm(d, A, B, C);
   }
   const GaussSrc no_gen{};
-  const int esize = prec == 1 ? 4 : 2;
+  const int kind = prec == 1 ? 1 : 2;  // kind::tf32 or kind::f16 (bf16)
+  const int ns = prec == 3 ? 3 : 2;    // slices per operand
+  const int esize = kind == 1 ? 4 : 2;
   const int kelem = KSLICE / esize;
   const int BN = TC_BN;
-  // a CTA pair per 256 x 128 tile when there are many such tiles (the last tile row is then
-  // less than half padding)
-  const bool pair = pairs_enabled() && M >= 1024;
-  const int tile_m = pair ? 2 * TC_BM : TC_BM;
-  const int64_t Mp = cdiv(M, tile_m) * tile_m, Np = cdiv(N, BN) * BN, Kp = cdiv(K, kelem) * kelem;
+  // CTA pairs are a candidate when there are many 256-row tiles (the last tile row is then
+  // less than half padding); the A panel is padded for them either way
+  const bool pair_ok = pairs_enabled() && M >= 1024;
+  const int64_t Mp = cdiv(M, pair_ok ? 2 * TC_BM : TC_BM) * (pair_ok ? 2 * TC_BM : TC_BM);
+  const int64_t Np = cdiv(N, BN) * BN, Kp = cdiv(K, kelem) * kelem;
   TATRG_CHECK(Mp < (int64_t(1) << 31) && Np < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: operand too large");
-  // packed operands (hi, lo) in one allocation
+  // packed operands (ns slices each) in one allocation
   const size_t abytes = size_t(Mp) * Kp * esize, bbytes = size_t(Np) * Kp * esize;
-  DevBuf pk(2 * abytes + 2 * bbytes, s);
+  DevBuf pk(ns * (abytes + bbytes), s);
   uint8_t* base = pk.as<uint8_t>();
-  void *ahi = base, *alo = base + abytes;
-  void *bhi = base + 2 * abytes, *blo = base + 2 * abytes + bbytes;
+  PackDst da{}, db{};
+  for (int p = 0; p < ns; ++p) {
+    da.p[p] = base + p * abytes;
+    db.p[p] = base + ns * abytes + p * bbytes;
+  }
+  auto pack = [&](const double* src, const DevModes& rm, const DevModes& km, int64_t R, int64_t tiles,
+                  const PackDst& dst, int rc, bool gen) {
+    const int grid = int(std::min<int64_t>(tiles, int64_t(sm_count()) * 6));
+    const int64_t kt = cdiv(Kp, PK_K);
+    const GaussSrc& gs = gen ? *gen_b : no_gen;
+    if (kind == 1 && gen) pack_kernel<1, 2, true><<<grid, 256, 0, s>>>(src, rm, km, R, K, Kp, kt, tiles, dst, rc, gs);
+    else if (kind == 1) pack_kernel<1, 2, false><<<grid, 256, 0, s>>>(src, rm, km, R, K, Kp, kt, tiles, dst, rc, gs);
+    else if (ns == 2 && gen) pack_kernel<2, 2, true><<<grid, 256, 0, s>>>(src, rm, km, R, K, Kp, kt, tiles, dst, rc, gs);
+    else if (ns == 2) pack_kernel<2, 2, false><<<grid, 256, 0, s>>>(src, rm, km, R, K, Kp, kt, tiles, dst, rc, gs);
+    else if (gen) pack_kernel<2, 3, true><<<grid, 256, 0, s>>>(src, rm, km, R, K, Kp, kt, tiles, dst, rc, gs);
+    else pack_kernel<2, 3, false><<<grid, 256, 0, s>>>(src, rm, km, R, K, Kp, kt, tiles, dst, rc, gs);
+    TATRG_CUDA(cudaGetLastError());
+  };
   {
     // A: rows = m (stride s0), k (stride s0);  B: rows = n (s0), k (s1)
     DevModes rm = dev(d.m), km = dev(d.k);
     const int rc = (d.m.n > 0 && d.m.s0[d.m.n - 1] == 1 && !(d.k.n > 0 && d.k.s0[d.k.n - 1] == 1)) ? 1 : 0;
-    const int64_t kt = cdiv(Kp, PK_K), ta = (Mp / PK_R) * kt;
-    const int ga = int(std::min<int64_t>(ta, int64_t(sm_count()) * 6));
-    if (prec == 1) pack_kernel<1, false><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc, no_gen);
-    else pack_kernel<2, false><<<ga, 256, 0, s>>>(A, rm, km, M, K, Kp, kt, ta, ahi, alo, rc, no_gen);
-    TATRG_CUDA(cudaGetLastError());
+    pack(A, rm, km, M, (Mp / PK_R) * cdiv(Kp, PK_K), da, rc, false);
     // a Gram (B is A read the same way) reuses A's panels
     bool same = !gen_b && (A == B) && Np == Mp && d.m.n == d.n.n && d.k.n > 0;
     for (int i = 0; same && i < d.m.n; ++i) same = d.m.ext[i] == d.n.ext[i] && d.m.s0[i] == d.n.s0[i];
     for (int i = 0; same && i < d.k.n; ++i) same = d.k.s0[i] == d.k.s1[i];
     if (same) {
-      bhi = ahi;
-      blo = alo;
-    }
-    DevModes rn = dev(d.n), kn = dev(d.k);
-    for (int i = 0; i < kMaxModes; ++i) kn.s0[i] = kn.s1[i];  // B's k strides
-    const int rcb = (d.n.n > 0 && d.n.s0[d.n.n - 1] == 1 && !(d.k.n > 0 && d.k.s1[d.k.n - 1] == 1)) ? 1 : 0;
-    const int64_t tb = (Np / PK_R) * kt;
-    const int gb = int(std::min<int64_t>(tb, int64_t(sm_count()) * 6));
-    if (!same) {
-      if (gen_b) {
-        if (prec == 1) pack_kernel<1, true><<<gb, 256, 0, s>>>(nullptr, rn, kn, N, K, Kp, kt, tb, bhi, blo, 0, *gen_b);
-        else pack_kernel<2, true><<<gb, 256, 0, s>>>(nullptr, rn, kn, N, K, Kp, kt, tb, bhi, blo, 0, *gen_b);
-      } else {
-        if (prec == 1) pack_kernel<1, false><<<gb, 256, 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb, no_gen);
-        else pack_kernel<2, false><<<gb, 256, 0, s>>>(B, rn, kn, N, K, Kp, kt, tb, bhi, blo, rcb, no_gen);
-      }
-      TATRG_CUDA(cudaGetLastError());
+      db = da;
+    } else {
+      DevModes rn = dev(d.n), kn = dev(d.k);
+      for (int i = 0; i < kMaxModes; ++i) kn.s0[i] = kn.s1[i];  // B's k strides
+      const int rcb = (d.n.n > 0 && d.n.s0[d.n.n - 1] == 1 && !(d.k.n > 0 && d.k.s1[d.k.n - 1] == 1)) ? 1 : 0;
+      pack(gen_b ? nullptr : B, rn, kn, N, (Np / PK_R) * cdiv(Kp, PK_K), db, gen_b ? 0 : rcb, gen_b != nullptr);
     }
   }
-  CUtensorMap mahi = make_map(ahi, Mp, Kp, esize, TC_BM, prec);
-  CUtensorMap malo = make_map(alo, Mp, Kp, esize, TC_BM, prec);
-  CUtensorMap mbhi = make_map(bhi, Np, Kp, esize, pair ? BN / 2 : BN, prec);
-  CUtensorMap mblo = make_map(blo, Np, Kp, esize, pair ? BN / 2 : BN, prec);
+  TcMaps maps1{}, maps2{};  // B boxes of a whole tile's columns (single CTAs) or half (pairs)
+  for (int p = 0; p < ns; ++p) {
+    maps1.a[p] = maps2.a[p] = make_map(da.p[p], Mp, Kp, esize, TC_BM, kind);
+    maps1.b[p] = make_map(db.p[p], Np, Kp, esize, BN, kind);
+    if (pair_ok) maps2.b[p] = make_map(db.p[p], Np, Kp, esize, BN / 2, kind);
+  }
   const int nkb = int(Kp / kelem);
-  const int64_t tiles = (Mp / tile_m) * (Np / BN);
-  int split = 1;
-  const int64_t workers = pair ? sm_count() / 2 : sm_count();  // CTAs or pairs
-  if (tiles < 2 * workers && nkb >= 8) split = int(std::min<int64_t>(cdiv(2 * workers, tiles), nkb / 4));
-  split = std::max(1, std::min(split, 512));
-  const int per = int(cdiv(nkb, split));
-  split = int(cdiv(nkb, per));
   TcArgs a;
   a.mC = dev(d.m);
   a.nC = dev(d.n);
   a.M = M;
   a.N = N;
-  a.kb_per_split = per;
   a.nkb = nkb;
   a.alpha = d.alpha;
   a.beta = d.beta;
-  a.atomic = split > 1 ? 1 : 0;
   {
     // C offset of column n equals n when the N modes chain contiguously in C
     bool contig = d.n.n >= 1 && d.n.s1[d.n.n - 1] == 1;
@@ -1016,21 +1114,44 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     a.n_contig = contig ? 1 : 0;
   }
   a.C = C;
-  if (split > 1) {
-    scale_c_kernel<<<int(std::min<int64_t>(cdiv(M * N, 256), 4096)), 256, 0, s>>>(C, dev(d.m), dev(d.n), M, N, d.beta);
-    TATRG_CUDA(cudaGetLastError());
-  }
-  a.mtiles = int(Mp / tile_m);
   a.ntiles = int(Np / BN);
-  a.split = split;
-  const int64_t units = int64_t(a.mtiles) * a.ntiles * split;
-  TATRG_CHECK(units < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: too many work units");
+  // one launch of configuration (pair, split): C is rewritten whole (zeroed first when K is
+  // split, the CTAs then add their partial sums)
+  auto run = [&](bool pair, int split) {
+    const int tile_m = pair ? 2 * TC_BM : TC_BM;
+    TcArgs g = a;
+    g.mtiles = int(cdiv(M, tile_m));
+    const int per = int(cdiv(nkb, split));
+    g.split = int(cdiv(nkb, per));
+    g.kb_per_split = per;
+    g.atomic = g.split > 1 ? 1 : 0;
+    if (g.split > 1) {
+      scale_c_kernel<<<int(std::min<int64_t>(cdiv(M * N, 256), 4096)), 256, 0, s>>>(C, dev(d.m), dev(d.n), M, N, d.beta);
+      TATRG_CUDA(cudaGetLastError());
+    }
+    const int64_t units = int64_t(g.mtiles) * g.ntiles * g.split;
+    TATRG_CHECK(units < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: too many work units");
+    const TcMaps& mp = pair ? maps2 : maps1;
+    if (prec == 1 && pair) launch<1, 2, true>(mp, g, units, s);
+    else if (prec == 1) launch<1, 2, false>(mp, g, units, s);
+    else if (prec == 2 && pair) launch<2, 2, true>(mp, g, units, s);
+    else if (prec == 2) launch<2, 2, false>(mp, g, units, s);
+    else if (pair) launch<2, 3, true>(mp, g, units, s);
+    else launch<2, 3, false>(mp, g, units, s);
+    return g.split;
+  };
+  // the split-K heuristic: enough work units for two per CTA (pair)
+  auto heuristic = [&](bool pair) {
+    const int64_t tiles = cdiv(M, pair ? 2 * TC_BM : TC_BM) * a.ntiles;
+    const int64_t workers = pair ? sm_count() / 2 : sm_count();
+    int split = 1;
+    if (tiles < 2 * workers && nkb >= 8) split = int(std::min<int64_t>(cdiv(2 * workers, tiles), nkb / 4));
+    return std::max(1, std::min(split, 512));
+  };
+  const TcChoice ch = tuned_choice(prec, M, N, K, a.n_contig, pair_ok, d.beta == 0.0, heuristic, run, s);
   const bool timed = st && st->timing;
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
-  if (prec == 1 && pair) launch<1, true>(mahi, malo, mbhi, mblo, a, units, s);
-  else if (prec == 1) launch<1, false>(mahi, malo, mbhi, mblo, a, units, s);
-  else if (pair) launch<2, true>(mahi, malo, mbhi, mblo, a, units, s);
-  else launch<2, false>(mahi, malo, mbhi, mblo, a, units, s);
+  const int split = run(ch.pair, ch.split);
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
   if (st) {
     st->launches += 3 + (split > 1);

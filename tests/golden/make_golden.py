@@ -27,16 +27,20 @@ CONFIGS = {
     "d4_chi10_h": (0.1497, 1e-4, 4, 10, 2, 2, 2, 10),
     "d2_chi16": (0.4, 0.0, 2, 16, 2, 2, 5, 24),
     "d3_chi8": (0.22, 0.01, 3, 8, 2, 2, 6, 12),
+    # chi = 24 with the multiplet gap of the library's split-precision steps (1e-6) from
+    # step 1: separates the rounding of the split forms from their cut rule
+    "c2_chi24_tau6": (0.1497, 0.0, 4, 24, 2, 2, 1, 40),
 }
+EXTRA = {"c2_chi24_tau6": {"split_tau": 1e-6, "split_from_step": 1}}
 
 
 def run(name):
     beta, h, d, chi, r, q, seed, steps = CONFIGS[name]
     t0 = time.time()
-    p = trg.Params(chi, r, q=q, seed=seed)
+    p = trg.Params(chi, r, q=q, seed=seed, **EXTRA.get(name, {}))
     R = trg.Run(beta, h, d, p)
     out = {"config": {"beta": beta, "h": h, "d": d, "chi": chi, "r": r, "q": q, "seed": seed,
-                      "steps": steps},
+                      "steps": steps, **EXTRA.get(name, {})},
            "lnc": [R.lnc[0]], "s": [R.s.tolist()], "sigma": [], "sq": [], "swap_gap": [],
            "sq_gap": [], "dims": [list(R.A.shape)], "lnz_after": []}
     for k in range(steps):
@@ -62,5 +66,5 @@ def run(name):
 
 
 if __name__ == "__main__":
-    for n in (sys.argv[1:] or CONFIGS):
+    for n in (sys.argv[1:] or [c for c in CONFIGS if c not in EXTRA]):
         run(n)

@@ -188,15 +188,17 @@ def _tc_case(torch, prec, M, N, K, mmodes, nmodes, kmodes, A, B, want, beta_C=No
     tg.contract(mmodes, nmodes, kmodes, _dev(torch, A), _dev(torch, B), C, beta=beta, precision=prec)
     torch.cuda.synchronize()
     got = C.cpu().numpy()
-    return np.max(np.abs(got - want)) / np.max(np.abs(want))
+    err = np.max(np.abs(got - want)) / np.max(np.abs(want))
+    print("precision %d: max relative error %.3e (M N K = %d %d %d)" % (prec, err, M, N, K))
+    return err
 
 
 # relative error bound of the split products: 3xTF32 keeps 22 mantissa bits per operand and
-# accumulates in FP32; the two-term BF16 split keeps 16
-TC_TOL = {tg.TF32X3: 5e-6, tg.BF16X3: 1e-4}
+# accumulates in FP32; the two-term BF16 split keeps 16, the three-term one 24
+TC_TOL = {tg.TF32X3: 5e-6, tg.BF16X3: 1e-4, tg.BF16X6: 5e-6}
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
 def test_contract_tensor_core_plain(torch, prec):
     rng = np.random.default_rng(11)
     M, N, K = 1000, 300, 517
@@ -206,7 +208,7 @@ def test_contract_tensor_core_plain(torch, prec):
     assert err < TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
 @pytest.mark.parametrize("M,N,K", [(1037, 300, 517), (1024, 256, 4096), (2500, 130, 64), (4099, 1000, 33)])
 def test_contract_tensor_core_cta_pair_tiles(torch, prec, M, N, K):
     """M >= 1024 takes 256 x 128 tiles on CTA pairs: ragged last tile rows and columns, a
@@ -221,7 +223,7 @@ def test_contract_tensor_core_cta_pair_tiles(torch, prec, M, N, K):
     assert err < TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
 def test_contract_tensor_core_cta_pair_multimode(torch, prec):
     """Permuted multi-mode operands and output on the CTA-pair path (M = 37 * 41 >= 1024)."""
     rng = np.random.default_rng(14)
@@ -236,7 +238,7 @@ def test_contract_tensor_core_cta_pair_multimode(torch, prec):
     assert err < TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
 def test_contract_tensor_core_multimode_beta(torch, prec):
     """Strided (permuted) operands and output, alpha/beta, ragged tiles in M, N and K."""
     rng = np.random.default_rng(12)
@@ -252,7 +254,7 @@ def test_contract_tensor_core_multimode_beta(torch, prec):
     assert err < TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
 def test_contract_tensor_core_split_k_gram(torch, prec):
     """A Gram Y^T Y with a long K split across CTAs (float64 atomic reduction)."""
     rng = np.random.default_rng(13)
@@ -264,7 +266,7 @@ def test_contract_tensor_core_split_k_gram(torch, prec):
     assert err < 10 * TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
 def test_sketch_generated_in_the_operand_packer(torch, prec):
     """W = R Omega with the Gaussian sketch drawn while the tensor-core operand is packed
     (float Box-Muller, never stored) against the oracle's product with its float64 sketch,

@@ -184,7 +184,7 @@ def test_fp64_runs_are_reproducible():
     assert np.array_equal(A0, A1) and np.array_equal(s0, s1) and np.array_equal(B0, B1)
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
 def test_split_precision_free_energy_within_1e8(prec):
     """chi = 24, 40 steps: with the split-precision contractions from step 13 on (the first
     twelve steps in FP64, where step k weighs 2^-k in ln Z / V), ln Z / V stays within
