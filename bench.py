@@ -257,9 +257,16 @@ C3_FILE = os.path.join(ROOT, "profiles", "c3_chi48_runs.json")
 
 
 def parse_form(text):
-    """'fp64', 'tf32x3@13' (split precision from step 13), 'bf16x3' (from step 1)."""
-    name, _, start = text.partition("@")
-    return name, int(start) if start else 1
+    """'fp64', 'tf32x3@13' (split precision from step 13), 'bf16x3' (from step 1),
+    'tf32x3@5/bf16x6:13' (FP64 steps 1-4, bf16x6 steps 5-12, tf32x3 from step 13).
+    Returns (name, start, early, late_from)."""
+    head, _, sched = text.partition("/")
+    name, _, start = head.partition("@")
+    early, late = None, 0
+    if sched:
+        early, _, late = sched.partition(":")
+        late = int(late)
+    return name, int(start) if start else 1, early, late
 
 
 def run_c3(args):
@@ -274,13 +281,14 @@ def run_c3(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     prec_of = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}
-    forms = [parse_form(f) for f in args.c3_forms.split(",")]
-    branch_at = sorted({k for name, k in forms if name != "fp64" and k > 1})
+    forms = [(f, parse_form(f)) for f in args.c3_forms.split(",")]
+    branch_at = sorted({k for _, (name, k, _, _) in forms if name != "fp64" and k > 1})
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def run(name, start, state=None):
+    def run(name, start, state=None, early=None, late=0, until=C3_STEPS):
         ctx = tg.Context(CHI, R, Q, seed=SEED, precision=prec_of[name], split_from_step=start,
-                         stream=stream)
+                         stream=stream, early_precision=prec_of[early] if early else 0,
+                         late_from_step=late)
         e0, e1 = ev(), ev()
         torch.cuda.synchronize()
         e0.record(stream)
@@ -291,11 +299,15 @@ def run_c3(args):
             A, s, B, k0, part = state
             ctx.set_state(A, s, B, k0, part)
         lnc, step_s, saved = [], [], {}
-        for k in range(k0 + 1, C3_STEPS + 1):
+
+        def keep(k):  # the FP64 state after step k - 1, where split forms branch off
+            torch.cuda.synchronize()
+            A, s, B = ctx.get_state()
+            saved[k] = (A, s, B, k - 1, ctx.step_info().partial_lnz if k > 1 else None)
+
+        for k in range(k0 + 1, until + 1):
             if state is None and k in branch_at:
-                torch.cuda.synchronize()
-                A, s, B = ctx.get_state()
-                saved[k] = (A, s, B, k - 1, ctx.step_info().partial_lnz if k > 1 else None)
+                keep(k)
             s0, s1 = ev(), ev()
             s0.record(stream)
             ctx.rg_step()
@@ -303,27 +315,40 @@ def run_c3(args):
             torch.cuda.synchronize()
             lnc.append(ctx.step_info().lnc)
             step_s.append(s0.elapsed_time(s1) / 1e3)
-        lnz = ctx.lnZ()
+        if state is None and until + 1 in branch_at:
+            keep(until + 1)
+        lnz = ctx.lnZ() if until == C3_STEPS else None
         e1.record(stream)
         torch.cuda.synchronize()
         ctx.close()
         return {"lnz": lnz, "lnc": lnc, "step_s": step_s}, saved
 
     out = {}
-    fp, saved = run("fp64", 1)
-    fp["run_s"] = sum(fp["step_s"])
-    out["fp64"] = dict(fp, precision="fp64", split_from_step=None)
-    print("fp64: lnZ/V = %.16f, %.1f s of steps" % (fp["lnz"], fp["run_s"]), flush=True)
-    for name, k in forms:
+    full_fp64 = any(name == "fp64" for _, (name, _, _, _) in forms)
+    if not full_fp64:
+        # reuse the stored whole FP64 run; recompute its trajectory only up to the last
+        # branch point (FP64 steps repeat bit for bit)
+        with open(C3_FILE) as f:
+            out = json.load(f)["runs"]
+        stop = max(branch_at) - 1 if branch_at else 0
+        fp, saved = run("fp64", 1, until=stop)
+        drift = max([abs(a - b) / max(1.0, abs(b)) for a, b in zip(fp["lnc"], out["fp64"]["lnc"][:stop])] + [0.0])
+        assert drift < 1e-11, "the FP64 trajectory did not repeat (%.2e)" % drift
+        fp = out["fp64"]
+    else:
+        fp, saved = run("fp64", 1)
+        fp["run_s"] = sum(fp["step_s"])
+        out["fp64"] = dict(fp, precision="fp64", split_from_step=None)
+        print("fp64: lnZ/V = %.16f, %.1f s of steps" % (fp["lnz"], fp["run_s"]), flush=True)
+    for tag, (name, k, early, late) in forms:
         if name == "fp64":
             continue
-        tag = "%s@%d" % (name, k)
-        res, _ = run(name, k, saved[k] if k > 1 else None)
+        res, _ = run(name, k, saved[k] if k > 1 else None, early, late)
         res["lnc"] = fp["lnc"][:k - 1] + res["lnc"]
         res["step_s"] = fp["step_s"][:k - 1] + res["step_s"]
         res["run_s"] = sum(res["step_s"])
         res["rel_to_fp64"] = abs(res["lnz"] - fp["lnz"]) / abs(fp["lnz"])
-        out[tag] = dict(res, precision=name, split_from_step=k)
+        out[tag] = dict(res, precision=name, split_from_step=k, early_precision=early, late_from_step=late)
         print("%s: lnZ/V = %.16f, rel %.3e, %.1f s of steps" % (tag, res["lnz"], res["rel_to_fp64"],
                                                                  res["run_s"]), flush=True)
     out["fp64"]["rel_to_fp64"] = 0.0

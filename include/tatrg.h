@@ -70,6 +70,9 @@ typedef struct {
   int profile;             /* 1: bracket every tensor-core GEMM with CUDA events and report
                               their device time in tatrg_step_info (tc_ms, tc_flops) */
   int sweep_workers;       /* temperatures tatrg_sweep runs concurrently (0: 8) */
+  int early_precision;     /* split precision of the steps split_from_step .. late_from_step-1
+                              (0: `precision`); e.g. TATRG_BF16X6 before TATRG_TF32X3 */
+  int late_from_step;      /* first step that uses `precision` (0: split_from_step) */
 } tatrg_params;
 
 /* Create a context on `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).

@@ -30,7 +30,8 @@ class Params(ctypes.Structure):
                 ("method", ctypes.c_int), ("precision", ctypes.c_int),
                 ("seed", ctypes.c_ulonglong), ("checkpoint_every", ctypes.c_int),
                 ("split_from_step", ctypes.c_int), ("split_stages", ctypes.c_int),
-                ("profile", ctypes.c_int), ("sweep_workers", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("sweep_workers", ctypes.c_int),
+                ("early_precision", ctypes.c_int), ("late_from_step", ctypes.c_int)]
 
 
 class StepInfo(ctypes.Structure):
@@ -115,9 +116,10 @@ class Context:
     """One RG run on the current CUDA device (tatrg_ctx)."""
 
     def __init__(self, chi, r, q=2, method=TRIAD, precision=FP64, seed=0, split_from_step=0,
-                 split_stages=0, profile=0, sweep_workers=0, stream=None):
+                 split_stages=0, profile=0, sweep_workers=0, stream=None, early_precision=0,
+                 late_from_step=0):
         self.params = Params(chi, r, q, method, precision, seed, 4, split_from_step, split_stages,
-                             profile, sweep_workers)
+                             profile, sweep_workers, early_precision, late_from_step)
         h = ctypes.c_void_p()
         _check(lib().tatrg_create(ctypes.byref(self.params), _stream_ptr(stream), ctypes.byref(h)))
         self._h = h

@@ -524,8 +524,10 @@ void tatrg_ctx::rg_step() {
   step++;
   const bool split = p.precision != TATRG_FP64 && step >= std::max(1, p.split_from_step);
   const int mask = p.split_stages ? p.split_stages : 31;
+  // precision schedule: FP64 before split_from_step, early_precision until late_from_step
+  const int prec_now = (p.early_precision != 0 && step < p.late_from_step) ? p.early_precision : p.precision;
   tau = split ? 1e-6 : 1e-10;
-  auto stage_prec = [&](Stage sg) { eng.prec = (split && (mask >> sg) & 1) ? p.precision : 0; };
+  auto stage_prec = [&](Stage sg) { eng.prec = (split && (mask >> sg) & 1) ? prec_now : 0; };
   stage_prec(ST_SWAP);
   cudaStream_t st = stream;
   StageTimer tm(st);
@@ -1411,6 +1413,8 @@ tatrg_status tatrg_create(const tatrg_params* params, void* cuda_stream, tatrg_c
                 "tatrg_create: unknown method");
     TATRG_CHECK(params->precision >= TATRG_FP64 && params->precision <= TATRG_BF16X6, TATRG_EINVAL,
                 "tatrg_create: unknown precision");
+    TATRG_CHECK(params->early_precision >= 0 && params->early_precision <= TATRG_BF16X6, TATRG_EINVAL,
+                "tatrg_create: unknown early precision");
     // The step's buffers come from the device's stream-ordered pool; keep freed blocks in
     // the pool across synchronisations instead of returning them to the driver each time.
     int dev = 0;

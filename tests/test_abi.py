@@ -38,7 +38,7 @@ def test_bad_arguments_fail_without_a_gpu(libpath):
     import paper_2412_14104_gb300 as tg
     L = tg.lib()
     h = ctypes.c_void_p()
-    bad = tg.Params(0, 2, 2, tg.TRIAD, tg.FP64, 0, 4, 0, 0, 0, 0)
+    bad = tg.Params(0, 2, 2, tg.TRIAD, tg.FP64, 0, 4, 0, 0, 0, 0, 0, 0)
     assert L.tatrg_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     assert b"chi" in L.tatrg_last_error(None)
     assert L.tatrg_rg_step(None, 1) == 1
