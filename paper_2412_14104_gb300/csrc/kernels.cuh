@@ -82,8 +82,8 @@ void tri_inverse(const double* R, int n, double* Rinv, cudaStream_t s);
 // S descending.  *status_dev = 0 converged, 1 not converged.
 void jacobi_svd(const double* A, int64_t m, int n, double* U, double* S, double* V,
                 int* status_dev, cudaStream_t s, Stats* st);
-// The same SVD through a column-pivoted QR, A P = Q R, and the Jacobi on R^T (square-ish
-// matrices: 32 <= n <= 160, m >= n, m n <= 25600).
+// The same SVD of a square matrix (32 <= n <= 160) through a column-pivoted QR of A^T and
+// the Jacobi on R^T.
 bool qrcp_svd_fits(int64_t m, int n);
 void jacobi_svd_qrcp(const double* A, int64_t m, int n, double* U, double* S, double* V,
                      int* status_dev, cudaStream_t s, Stats* st);

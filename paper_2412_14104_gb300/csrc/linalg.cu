@@ -827,11 +827,13 @@ void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S,
   TATRG_CUDA(cudaStreamSynchronize(s));
 }
 
-// SVD through a pivoted QR (Drmac & Veselic, SIAM J. Matrix Anal. Appl. 29, 2008): A P = Q R,
-// then one-sided Jacobi on X = R^T, X = Ux S Vx^T, so A = (Q Vx) S (P Ux)^T.  Pivoting puts the
-// large columns first, and the rows of R are graded, so the Jacobi sweeps on R^T converge in
-// a few sweeps where the Jacobi on A takes tens.
-bool qrcp_svd_fits(int64_t m, int n) { return n >= 32 && n <= kQrcpMaxN && m >= n && m * n <= kQrcpMaxElems; }
+// SVD of a square A through a pivoted QR of its transpose (Drmac & Veselic, SIAM J. Matrix
+// Anal. Appl. 29, 2008): A^T P = Q R, then one-sided Jacobi on X = R^T, X = Ux S Vx^T, so
+// A = P X Q^T = (P Ux) S (Q Vx)^T.  Pivoting puts the large columns first and the rows of R
+// are graded, so the Jacobi sweeps on R^T converge in a few sweeps where the Jacobi on A
+// takes tens.  Factoring A^T keeps the conventions of jacobi_svd: V is a full orthonormal
+// basis and the columns of U that belong to zero singular values are zero.
+bool qrcp_svd_fits(int64_t m, int n) { return n >= 32 && n <= kQrcpMaxN && m == n; }
 
 void jacobi_svd_qrcp(const double* A, int64_t m, int n, double* U, double* S, double* V, int* status_dev,
                      cudaStream_t s, Stats* st) {
@@ -839,19 +841,21 @@ void jacobi_svd_qrcp(const double* A, int64_t m, int n, double* U, double* S, do
   check_extent(A, m * n - 1, sizeof(double), "qrcp input");
   check_extent(U, m * n - 1, sizeof(double), "qrcp U");
   check_extent(V, int64_t(n) * n - 1, sizeof(double), "qrcp V");
-  DevBuf X(size_t(n) * n * sizeof(double), s), Qm(size_t(m) * n * sizeof(double), s),
-      perm(size_t(n) * sizeof(int), s), Ux(size_t(n) * n * sizeof(double), s), Vx(size_t(n) * n * sizeof(double), s);
+  DevBuf At(size_t(n) * n * sizeof(double), s), X(size_t(n) * n * sizeof(double), s),
+      Qm(size_t(n) * n * sizeof(double), s), perm(size_t(n) * sizeof(int), s),
+      Ux(size_t(n) * n * sizeof(double), s), Vx(size_t(n) * n * sizeof(double), s);
+  transpose(A, n, n, At.d(), s);
   ensure_smem_attr(reinterpret_cast<const void*>(qrcp_kernel), int(kQrcpMaxElems * sizeof(double)));
-  qrcp_kernel<<<1, 1024, size_t(m) * n * sizeof(double), s>>>(A, int(m), n, X.d(), Qm.d(), perm.as<int>());
+  qrcp_kernel<<<1, 1024, size_t(n) * n * sizeof(double), s>>>(At.d(), n, n, X.d(), Qm.d(), perm.as<int>());
   TATRG_CUDA(cudaGetLastError());
   jacobi_svd(X.d(), n, n, Ux.d(), S, Vx.d(), status_dev, s, st);
-  GemmDesc g;  // U = Q Vx
-  g.m = modes({{m, n, n}});
+  GemmDesc g;  // V = Q Vx
+  g.m = modes({{n, n, n}});
   g.n = modes({{n, 1, 1}});
   g.k = modes({{n, 1, n}});
-  gemm_f64(g, Qm.d(), Vx.d(), U, s, st);
+  gemm_f64(g, Qm.d(), Vx.d(), V, s, st);
   permute_rows_kernel<<<int(std::max<int64_t>(1, std::min<int64_t>(cdiv(int64_t(n) * n, 256), 64))), 256, 0, s>>>(
-      Ux.d(), perm.as<int>(), n, V);
+      Ux.d(), perm.as<int>(), n, U);  // U[perm[j], :] = Ux[j, :]
   TATRG_CUDA(cudaGetLastError());
   if (st) st->launches += 2;
 }

@@ -464,16 +464,22 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
             if (!mbar_wait(&full_bar[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
             if (PAIR && !mbar_wait<true>(&peer_full[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
             tc_fence_after();
-            const uint32_t base = smem_u32(smem + s * STAGE);
+            // descriptors of the stage's slices, formed once (the issuing thread is on the
+            // critical path of every MMA)
+            const uint64_t d0 = sdesc_sw(smem_u32(smem + s * STAGE));
+            uint64_t ad[NS], bd[NS];
+#pragma unroll
+            for (int p = 0; p < NS; ++p) {
+              ad[p] = d0 + uint64_t((p * A_TILE) >> 4);
+              bd[p] = d0 + uint64_t((NS * A_TILE + p * B_TILE) >> 4);
+            }
 #pragma unroll
             for (int kk = 0; kk < KSLICE / 32; ++kk) {  // 32 bytes of K per instruction
               const uint64_t off = uint64_t(kk * 2);
 #pragma unroll
-              for (int t = 0; t < Products<NS>::n; ++t) {
-                const uint64_t ad = sdesc_sw(base + Products<NS>::a(t) * A_TILE) + off;
-                const uint64_t bd = sdesc_sw(base + NS * A_TILE + Products<NS>::b(t) * B_TILE) + off;
-                mma<PREC, CG>(acc, ad, bd, id, (i > c * KC || kk > 0 || t > 0) ? 1u : 0u);
-              }
+              for (int t = 0; t < Products<NS>::n; ++t)
+                mma<PREC, CG>(acc, ad[Products<NS>::a(t)] + off, bd[Products<NS>::b(t)] + off, id,
+                              (i > c * KC || kk > 0 || t > 0) ? 1u : 0u);
             }
             mma_commit<CG>(&empty_bar[s]);
           }
@@ -886,8 +892,8 @@ void launch(const TcMaps& maps, const TcArgs& a, int64_t units, cudaStream_t s) 
   constexpr int STAGE = stage_bytes<NS, PAIR>();
   constexpr int STAGES = SMEM_BUDGET / STAGE;
   static_assert(STAGES >= 2, "the ring needs two stages");
-  constexpr int KC = TATRG_CHAIN_K / (PREC == 1 ? KSLICE / 4 : KSLICE / 2);  // stages per FP32 chain
-  static_assert(KC >= 1, "an FP32 chain spans at least one stage");
+  constexpr int KC_ = TATRG_CHAIN_K / (PREC == 1 ? KSLICE / 4 : KSLICE / 2);  // stages per FP32 chain
+  constexpr int KC = KC_ > 0 ? KC_ : 1;  // at least one stage
   constexpr int SMEM = STAGES * STAGE + 1024;
   auto k = tc_gemm_kernel<PREC, NS, KC, STAGES, 2, PAIR>;
   const int resident = resident_units<PREC, NS, PAIR>(reinterpret_cast<const void*>(k), SMEM);

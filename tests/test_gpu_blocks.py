@@ -109,9 +109,9 @@ def test_jacobi_svd(torch, m, n):
     assert np.allclose(v.T @ v, np.eye(n), atol=1e-13)
 
 
-@pytest.mark.parametrize("m,n,spread", [(144, 144, 1e-12), (160, 100, 1e-6), (144, 144, 1.0), (120, 32, 1e-9)])
+@pytest.mark.parametrize("m,n,spread", [(144, 144, 1e-12), (160, 160, 1e-6), (144, 144, 1.0), (32, 32, 1e-9)])
 def test_svd_through_pivoted_qr(torch, m, n, spread):
-    """Square-ish SVDs (32 <= n <= 160) take the pivoted-QR-preconditioned Jacobi: singular
+    """Square SVDs (32 <= n <= 160) take the pivoted-QR-preconditioned Jacobi: singular
     values spread over 1 .. spread (graded, like the Gram spectra of the step), random
     singular vectors; against NumPy and the reconstruction."""
     rng = np.random.default_rng(int(m + n + 1 / spread) % 1000)
@@ -130,6 +130,24 @@ def test_svd_through_pivoted_qr(torch, m, n, spread):
     assert np.allclose((u * s) @ v.T, A, atol=1e-13 * s_ref[0])
     assert np.allclose(v.T @ v, np.eye(n), atol=1e-13)
     assert np.allclose(u.T @ u, np.eye(n), atol=1e-11 if spread >= 1e-6 else 1e-3)
+
+
+def test_svd_conventions_on_a_rank_deficient_square_matrix(torch):
+    """Rank 50 of 100: V is a full orthonormal basis and the columns of U that belong to the
+    zero singular values are zero, on the pivoted-QR path as on the plain one (the tangent
+    rules rely on it)."""
+    rng = np.random.default_rng(17)
+    n, k = 100, 50
+    A = rng.standard_normal((n, k)) @ rng.standard_normal((k, n))
+    U = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    S = torch.empty(n, dtype=torch.float64, device="cuda")
+    V = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    tg.svd(_dev(torch, A), U, S, V)
+    u, s, v = U.cpu().numpy(), S.cpu().numpy(), V.cpu().numpy()
+    assert np.allclose(v.T @ v, np.eye(n), atol=1e-13)
+    assert np.allclose((u * s) @ v.T, A, atol=1e-12 * s[0])
+    assert np.allclose(u[:, :k].T @ u[:, :k], np.eye(k), atol=1e-12)
+    assert np.max(np.abs(u[:, s < 1e-12 * s[0]])) < 1e-12 or np.all(s[k:] > 1e-12 * s[0])
 
 
 def test_orth_full_rank_and_rank_deficient(torch):
