@@ -280,7 +280,7 @@ def run_c3(args):
     import paper_2412_14104_gb300 as tg
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    prec_of = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}
+    prec_of = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "ozaki": tg.OZAKI, "fp64": tg.FP64}
     forms = [(f, parse_form(f)) for f in args.c3_forms.split(",")]
     branch_at = sorted({k for _, (name, k, _, _) in forms if name != "fp64" and k > 1})
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -387,7 +387,7 @@ def run_methods(args):
     import paper_2412_14104_gb300 as tg
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}[args.precision]
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "ozaki": tg.OZAKI, "fp64": tg.FP64}[args.precision]
     chis = [int(c) for c in args.methods_chis.split(",")]
     r = 7
     rows = {}
@@ -496,7 +496,7 @@ def run_c4(args):
     stream = torch.cuda.current_stream()
     betas = 0.145 + np.arange(64) * (0.01 / 63)
     chi, r, steps, seed = 32, 2, 32, 3
-    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}[args.precision]
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "ozaki": tg.OZAKI, "fp64": tg.FP64}[args.precision]
     ctx = tg.Context(chi, r, Q, seed=seed, precision=prec, sweep_workers=args.sweep_workers, stream=stream)
     ctx.sweep_observables(betas[:2], 0.0, 4, steps)  # first-use setup (tuning of the shapes)
     torch.cuda.synchronize()
@@ -548,7 +548,7 @@ def run_d3(args):
     import paper_2412_14104_gb300 as tg
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
-    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}[args.precision]
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "ozaki": tg.OZAKI, "fp64": tg.FP64}[args.precision]
     rows = {}
     for chi in [int(c) for c in args.d3_chis.split(",")]:
         ctx = tg.Context(chi, 2, Q, seed=6, precision=prec, split_from_step=13, stream=stream)
@@ -579,7 +579,7 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "fp64": tg.FP64}[args.precision]
+    prec = {"tf32x3": tg.TF32X3, "bf16x3": tg.BF16X3, "bf16x6": tg.BF16X6, "ozaki": tg.OZAKI, "fp64": tg.FP64}[args.precision]
     seed = SEED + 1000 * rank
     chi, r = args.chi, args.r
     ctx = tg.Context(chi, r, Q, seed=seed, precision=prec, profile=1, stream=stream)
@@ -647,7 +647,7 @@ def run_ours(args, world, rank, local):
     # achieved: algorithmic flops (2 M N K per contraction) over the kernel's device time;
     # the split forms issue 3 (6 for bf16x6) tensor-core products per algorithmic one
     achieved = tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
-    nprod = 6.0 if prec == tg.BF16X6 else 3.0
+    nprod = {tg.BF16X6: 6.0, tg.OZAKI: 15.0}.get(prec, 3.0)
     traffic = None  # DRAM bytes per launch from the committed ncu capture of this workload
     prof = os.path.join(ROOT, "profiles", "tc_gemm_chi48_traffic.json")
     if os.path.exists(prof) and (chi, r) == (CHI, R) and prec == tg.TF32X3:
@@ -737,7 +737,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "bf16x6", "fp64"])
+    ap.add_argument("--precision", default="tf32x3", choices=["tf32x3", "bf16x3", "bf16x6", "ozaki", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-delta-f", action="store_true")

@@ -50,9 +50,14 @@ typedef enum {
   TATRG_FP64 = 0,   /* float64 CUDA-core GEMMs */
   TATRG_TF32X3 = 1, /* tcgen05 kind::tf32, operands split hi+lo, 3 products, FP32 accumulate */
   TATRG_BF16X3 = 2, /* tcgen05 kind::f16 with bf16 hi+lo split, 3 products, FP32 accumulate */
-  TATRG_BF16X6 = 3  /* tcgen05 kind::f16 with bf16 hi+mid+lo split (the 24 bits of the float
+  TATRG_BF16X6 = 3, /* tcgen05 kind::f16 with bf16 hi+mid+lo split (the 24 bits of the float
                        nearest to each operand), the 6 products down to 2^-16 of hi*hi,
                        FP32 accumulate: the tensor time of TATRG_TF32X3 at float accuracy */
+  TATRG_OZAKI = 4   /* float64-grade: each operand row (column) scaled by a power of two and
+                       cut into five 7-bit integer slices (Ozaki et al. 2012), the 15 slice
+                       products of weight >= 2^-28 on tcgen05 kind::f16 with exact FP32
+                       sums over chunks of 512, combined in double-float: ~2^-36 relative
+                       to the largest entries of the rows and columns involved */
 } tatrg_precision;
 
 typedef struct {

@@ -13,7 +13,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtatrg.so")
 
-FP64, TF32X3, BF16X3, BF16X6 = 0, 1, 2, 3
+FP64, TF32X3, BF16X3, BF16X6, OZAKI = 0, 1, 2, 3, 4
 ATRG, TRIAD = 0, 1
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENUMERIC", 5: "ETIMEOUT",
            6: "ESTATE", 7: "ENOTIMPL"}

@@ -21,12 +21,13 @@ static bool use_tc(const Engine& e, const GemmDesc& d) {
 }
 
 void Engine::gemm(const GemmDesc& d, const double* A, const double* B, double* C) {
-  if (use_tc(*this, d)) gemm_tc(d, A, B, C, prec, s_, &st_);
+  if (use_tc(*this, d) && prec == 4) gemm_oz(d, A, B, C, s_, &st_);
+  else if (use_tc(*this, d)) gemm_tc(d, A, B, C, prec, s_, &st_);
   else gemm_f64(d, A, B, C, s_, &st_);
 }
 
 bool Engine::gemm_gauss_b(const GemmDesc& d, const double* A, const GaussSrc& g, double* C) {
-  if (!use_tc(*this, d)) return false;
+  if (!use_tc(*this, d) || prec == 4) return false;  // the Ozaki slices read a stored sketch
   gemm_tc(d, A, nullptr, C, prec, s_, &st_, &g);
   return true;
 }
@@ -104,14 +105,14 @@ OrthResult Engine::orth(const double* Y, int64_t m, int64_t n) {
   if (m >= n) {
     // FP64 Grams: plain CholeskyQR2.  Split-precision Grams carry ~1e-7 relative error, so
     // their first pass is shifted (shifted CholeskyQR3).
-    r = cholqr2(Y, m, n, prec == 0 ? 0.0 : 1e-6, ok);
+    r = cholqr2(Y, m, n, fp64_grade() ? 0.0 : 1e-6, ok);
     if (ok) return r;
   }
   // Rank-revealing fallback: one-sided Jacobi SVD of Y itself (no squared condition
   // number), Y = U S V^T; keep the directions above the rounding floor: Q = U_k,
   // R = S_k V_k^T.
   SvdResult e = svd(Y, m, n);
-  const double cut = prec == 0 ? 1e-14 : 1e-7;
+  const double cut = fp64_grade() ? 1e-14 : 1e-7;
   int k = keep_count(e.s, cut, std::min(m, n));
   TATRG_CHECK(k >= 1, TATRG_ENUMERIC, "orth: zero matrix");
   OrthResult out;
@@ -130,8 +131,8 @@ OrthResult Engine::orth(const double* Y, int64_t m, int64_t n) {
 
 Engine::MetricOrth Engine::orth_metric(const double* X, int64_t nin, int64_t w, const Op& metric) {
   MetricOrth out;
-  const int passes = prec == 0 ? 2 : 3;
-  const double shift = prec == 0 ? 0.0 : 1e-6;
+  const int passes = fp64_grade() ? 2 : 3;
+  const double shift = fp64_grade() ? 0.0 : 1e-6;
   DevBuf G(w * w * sizeof(double), s_), Rk(w * w * sizeof(double), s_), Ri(w * w * sizeof(double), s_),
       Racc(w * w * sizeof(double), s_), Rtmp(w * w * sizeof(double), s_);
   DMat cur;

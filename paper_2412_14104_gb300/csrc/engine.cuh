@@ -35,8 +35,10 @@ class Engine {
   cudaStream_t stream() const { return s_; }
   Stats& stats() { return st_; }
 
-  // precision of the large contractions (0 = FP64, 1 = 3xTF32, 2 = BF16x3)
+  // precision of the large contractions (0 = FP64, 1 = 3xTF32, 2 = BF16x3, 3 = BF16x6,
+  // 4 = Ozaki slices); FP64 and the Ozaki slices are float64-grade, the others float-grade
   int prec = 0;
+  bool fp64_grade() const { return prec == 0 || prec == 4; }
   bool allow_tc = true;
 
   void gemm(const GemmDesc& d, const double* A, const double* B, double* C);

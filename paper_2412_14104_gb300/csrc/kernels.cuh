@@ -111,5 +111,9 @@ struct GaussSrc {
 // gen_b: B is that sketch (B must be null)
 void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int prec,
              cudaStream_t s, Stats* st, const GaussSrc* gen_b = nullptr);
+// The float64-grade contraction from exact tensor-core products of integer slices
+// (TATRG_OZAKI).
+void gemm_oz(const GemmDesc& d, const double* A, const double* B, double* C, cudaStream_t s,
+             Stats* st);
 
 }  // namespace tatrg

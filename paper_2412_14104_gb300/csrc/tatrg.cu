@@ -385,7 +385,7 @@ DMat tatrg_ctx::isometry(Engine& E, const double* rho, int64_t Gd, int kind, std
     if (rhod) et = E.svd_tan(rhod, Gd, Gd, e, keep_count(e.s, 1e-14, k), multiplet_groups(e.s, tau));
   } else {
     DevBuf om(Gd * k * sizeof(double), stream);
-    gaussian(p.seed, stream_id(step, kind), replica, Gd * k, om.d(), stream, E.prec != 0);
+    gaussian(p.seed, stream_id(step, kind), replica, Gd * k, om.d(), stream, !E.fp64_grade());
     if (rhod) {
       Engine::RsvdT r = E.rsvd_psd_t(rho, rhod, Gd, k, p.q, om.d(), tau);
       e = std::move(r.e);
@@ -424,7 +424,7 @@ void tatrg_ctx::factor(Engine& E, const double* rho, int64_t P, int kind, DMat& 
     if (rhod) et = E.svd_tan(rhod, P, P, e, keep_count(e.s, 1e-14, ell), multiplet_groups(e.s, tau));
   } else {
     DevBuf om(P * ell * sizeof(double), stream);
-    gaussian(p.seed, stream_id(step, kind), replica, P * ell, om.d(), stream, E.prec != 0);
+    gaussian(p.seed, stream_id(step, kind), replica, P * ell, om.d(), stream, !E.fp64_grade());
     if (rhod) {
       Engine::RsvdT r = E.rsvd_psd_t(rho, rhod, P, ell, p.q, om.d(), tau);
       e = std::move(r.e);
@@ -526,7 +526,8 @@ void tatrg_ctx::rg_step() {
   const int mask = p.split_stages ? p.split_stages : 31;
   // precision schedule: FP64 before split_from_step, early_precision until late_from_step
   const int prec_now = (p.early_precision != 0 && step < p.late_from_step) ? p.early_precision : p.precision;
-  tau = split ? 1e-6 : 1e-10;
+  // multiplet gap: above the rounding of the float-grade forms, the oracle's 1e-10 otherwise
+  tau = (split && prec_now != TATRG_OZAKI) ? 1e-6 : 1e-10;
   auto stage_prec = [&](Stage sg) { eng.prec = (split && (mask >> sg) & 1) ? prec_now : 0; };
   stage_prec(ST_SWAP);
   cudaStream_t st = stream;
@@ -613,7 +614,7 @@ void tatrg_ctx::rg_step() {
     auto materialise = [&]() {
       if (!om.empty()) return;
       om = DevBuf(rows * ell * sizeof(double), st);
-      gaussian(swap_sketch.seed, swap_sketch.sid, swap_sketch.replica, rows * ell, om.d(), st, eng.prec != 0);
+      gaussian(swap_sketch.seed, swap_sketch.sid, swap_sketch.replica, rows * ell, om.d(), st, !eng.fp64_grade());
     };
     // M X: W[a,k,b,p] = sum_j Bs[a,k,j] X[(b,j),p];  Y[(a,i),p] = sum_{k,b} As[k,i,b] W[a,k,b,p]
     // (with any pair of factors Ap, Bp in place of As, Bs; beta = 1 accumulates into Y)
@@ -1411,9 +1412,9 @@ tatrg_status tatrg_create(const tatrg_params* params, void* cuda_stream, tatrg_c
                 "tatrg_create: need chi >= 1, r >= 1, q >= 0");
     TATRG_CHECK(params->method == TATRG_ATRG || params->method == TATRG_TRIAD, TATRG_EINVAL,
                 "tatrg_create: unknown method");
-    TATRG_CHECK(params->precision >= TATRG_FP64 && params->precision <= TATRG_BF16X6, TATRG_EINVAL,
+    TATRG_CHECK(params->precision >= TATRG_FP64 && params->precision <= TATRG_OZAKI, TATRG_EINVAL,
                 "tatrg_create: unknown precision");
-    TATRG_CHECK(params->early_precision >= 0 && params->early_precision <= TATRG_BF16X6, TATRG_EINVAL,
+    TATRG_CHECK(params->early_precision >= 0 && params->early_precision <= TATRG_OZAKI, TATRG_EINVAL,
                 "tatrg_create: unknown early precision");
     // The step's buffers come from the device's stream-ordered pool; keep freed blocks in
     // the pool across synchronisations instead of returning them to the driver each time.
@@ -1705,7 +1706,7 @@ tatrg_status tatrg_contract(const tatrg_contraction* c, int precision, const dou
                             double* C, void* stream) {
   return guard(nullptr, [&] {
     TATRG_CHECK(c && A && B && C, TATRG_EINVAL, "tatrg_contract: null argument");
-    TATRG_CHECK(precision >= 0 && precision <= 3, TATRG_EINVAL, "tatrg_contract: bad precision");
+    TATRG_CHECK(precision >= 0 && precision <= 4, TATRG_EINVAL, "tatrg_contract: bad precision");
     GemmDesc g;
     g.m = modes({{c->m_ext[0], c->m_sA[0], c->m_sC[0]}, {c->m_ext[1], c->m_sA[1], c->m_sC[1]},
                  {c->m_ext[2], c->m_sA[2], c->m_sC[2]}, {c->m_ext[3], c->m_sA[3], c->m_sC[3]}});
@@ -1732,7 +1733,7 @@ tatrg_status tatrg_orth(int precision, int64_t m, int64_t n, const double* Y, do
                         int* k, void* stream) {
   return guard(nullptr, [&] {
     TATRG_CHECK(Y && Q && R && k && m >= n && n >= 1 && n <= 1024, TATRG_EINVAL, "tatrg_orth: bad argument");
-    TATRG_CHECK(precision >= 0 && precision <= 3, TATRG_EINVAL, "tatrg_orth: bad precision");
+    TATRG_CHECK(precision >= 0 && precision <= 4, TATRG_EINVAL, "tatrg_orth: bad precision");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     Engine e(s);
     e.prec = precision;

@@ -218,6 +218,19 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// 8 columns of 32 lanes
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                 "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
 
 // Instruction descriptor for kind::tf32 (A/B format 2) or kind::f16 with bf16 (format 1),
 // FP32 accumulator, both operands K-major, M = 128.
@@ -832,19 +845,453 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-CUtensorMap make_map(void* base, int64_t rows, int64_t kp, int esize, int box_rows, int prec) {
+CUtensorMap make_map(void* base, int64_t rows, int64_t kp, int esize, int box_rows, int prec,
+                     int kslice = KSLICE) {
   CUtensorMap m;
   cuuint64_t dims[2] = {cuuint64_t(kp), cuuint64_t(rows)};
   cuuint64_t strides[1] = {cuuint64_t(kp * esize)};
-  cuuint32_t box[2] = {cuuint32_t(KSLICE / esize), cuuint32_t(box_rows)};
+  cuuint32_t box[2] = {cuuint32_t(kslice / esize), cuuint32_t(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode_fn()(&m, prec == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
                            2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           KSLICE == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                           kslice == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   TATRG_CHECK(r == CUDA_SUCCESS, TATRG_ECUDA, "cuTensorMapEncodeTiled failed");
   return m;
+}
+
+// ---------------------------------------------------------------------------------
+// Near-FP64 contractions from exact tensor-core products: the error-free splitting of a
+// matrix product into products of slices (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms
+// 59, 2012), with bf16 slices and FP32 accumulation.  Every row of A (every column of B)
+// is scaled by 2^-e, e the exponent of its largest entry, and written as OZ_NS balanced
+// base-2^7 digits: x = 2^e sum_{s=1..5} a_s 2^(-7s) + O(2^(e-36)), |a_1| <= 128,
+// |a_s| <= 64 otherwise.  Slice s is stored as a_s 2^(-7(s-1)) (exact in bf16), so a slice
+// product of level s + t carries the weight 2^(-7(s+t-2)) of its level.  Over a chunk of
+// OZ_CHUNK K elements the level-2 product sum is an integer below 2^24, and the level-3
+// sum a multiple of 2^-7 below 2^16: both exact in the FP32 accumulator.  The 15 products
+// with s + t <= 6 are kept: levels 2 and 3 in one exact accumulator each, levels 4..6
+// together (that sum is ~2^-14 of the result, so its float rounding is ~2^-38 relative).
+// Each chunk is combined exactly (TwoSum) and added into double-float sums in tensor
+// memory; the output is alpha 2^(e_row + e_col - 14) (hi + lo).
+constexpr int OZ_NS = 5;                       // slices per operand
+constexpr int OZ_BN = 64;                      // output columns per tile
+constexpr int OZ_KS = 64;                      // bytes of K per stage row (SWIZZLE_64B)
+constexpr int OZ_KELEM = OZ_KS / 2;            // bf16 K elements per stage
+constexpr int OZ_STAGES = 3;
+constexpr int OZ_CHUNK = 512;                  // 2 * 2^13 * 512 < 2^24: level-3 sums stay exact
+constexpr int OZ_KC = OZ_CHUNK / OZ_KELEM;     // stages per chunk
+constexpr int OZ_A_TILE = TC_BM * OZ_KS;       // bytes
+constexpr int OZ_B_TILE = OZ_BN * OZ_KS;
+constexpr int OZ_STAGE = OZ_NS * (OZ_A_TILE + OZ_B_TILE);
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024;
+constexpr int OZ_EXP_NONE = -1061109568;       // exponent of an all-zero row (bytes 0xC0)
+
+// slice indices (0 = most significant) and accumulator of product t, smallest level first
+__device__ __forceinline__ constexpr int oz_a(int t) {
+  return t == 0 ? 4 : t == 1 ? 0 : t == 2 ? 3 : t == 3 ? 1 : t == 4 ? 2 : t == 5 ? 3 : t == 6 ? 0 : t == 7 ? 2
+       : t == 8 ? 1 : t == 9 ? 2 : t == 10 ? 0 : t == 11 ? 1 : t == 12 ? 1 : 0;
+}
+__device__ __forceinline__ constexpr int oz_b(int t) {
+  return t == 0 ? 0 : t == 1 ? 4 : t == 2 ? 1 : t == 3 ? 3 : t == 4 ? 2 : t == 5 ? 0 : t == 6 ? 3 : t == 7 ? 1
+       : t == 8 ? 2 : t == 9 ? 0 : t == 10 ? 2 : t == 11 ? 1 : t == 12 ? 0 : t == 13 ? 1 : 0;
+}
+__device__ __forceinline__ constexpr int oz_acc(int t) { return t < 12 ? 2 : t < 14 ? 1 : 0; }
+__device__ __forceinline__ constexpr bool oz_first(int t) { return t == 0 || t == 12 || t == 14; }
+
+// K-major operand tile with 64-byte rows, SWIZZLE_64B (8-row atoms of 512 bytes)
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFF) >> 4);
+  d |= uint64_t(1) << 16;
+  d |= uint64_t((8 * OZ_KS) >> 4) << 32;
+  d |= uint64_t(1) << 46;
+  d |= uint64_t(4) << 61;  // SWIZZLE_64B
+  return d;
+}
+
+// frexp exponent of a nonzero finite double from its bits (|x| < 2^e, e the result)
+__device__ __forceinline__ int oz_exponent(double x) {
+  const uint64_t b = uint64_t(__double_as_longlong(x));
+  const int ex = int((b >> 52) & 0x7FF);
+  return ex == 0 ? OZ_EXP_NONE : ex - 1022;  // zero and subnormals count as zero
+}
+
+// the five balanced base-2^7 digits of x 2^(35 - e) rounded to an integer (integer
+// arithmetic on the IEEE fields: this GPU has few FP64 units)
+__device__ __forceinline__ void oz_digits(double x, int e, int (&d)[OZ_NS]) {
+  const uint64_t b = uint64_t(__double_as_longlong(x));
+  const int ex = int((b >> 52) & 0x7FF);
+#pragma unroll
+  for (int s = 0; s < OZ_NS; ++s) d[s] = 0;
+  if (ex == 0 || e == OZ_EXP_NONE) return;
+  const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (uint64_t(1) << 52);  // |x| = M 2^(ex - 1075)
+  const int sh = 1040 - ex + e;                                          // >= 18 since |x| < 2^e
+  int64_t F = sh >= 63 ? 0 : int64_t((M + (uint64_t(1) << (sh - 1))) >> sh);
+  if (b >> 63) F = -F;
+#pragma unroll
+  for (int s = OZ_NS - 1; s > 0; --s) {
+    const int64_t dd = ((F + 64) & 127) - 64;
+    d[s] = int(dd);
+    F = (F - dd) >> 7;
+  }
+  d[0] = int(F);
+}
+
+// Largest exponent of every row of a multi-mode operand (rows rm, K km): one block per
+// strip of PK_R rows x PK_K K elements (grid-stride); row-contiguous sources are read with
+// the lanes along the rows, the others with the lanes along K.
+__global__ void __launch_bounds__(256) oz_exp_kernel(const double* __restrict__ src, DevModes rm, DevModes km,
+                                                     int64_t R, int64_t K, int64_t ktiles, int64_t ntiles,
+                                                     int* __restrict__ exps, int r_contig) {
+  __shared__ int64_t roff[PK_R], koff[PK_K];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = (t / ktiles) * PK_R, k0 = (t % ktiles) * PK_K;
+    __syncthreads();
+    if (tid < PK_R) {
+      int64_t a = 0, c = 0;
+      if (r0 + tid < R) mode_offsets(rm, r0 + tid, a, c);
+      roff[tid] = a;
+    } else if (tid < PK_R + PK_K) {
+      const int j = tid - PK_R;
+      int64_t a = 0, c = 0;
+      if (k0 + j < K) mode_offsets(km, k0 + j, a, c);
+      koff[j] = a;
+    }
+    __syncthreads();
+    if (r_contig) {  // lane = row; warp w takes K elements w, w + 8, ...
+      int m = OZ_EXP_NONE;
+      if (r0 + lane < R)
+        for (int kk = warp; kk < PK_K && k0 + kk < K; kk += 8) m = max(m, oz_exponent(__ldg(src + roff[lane] + koff[kk])));
+      if (m != OZ_EXP_NONE) atomicMax(exps + r0 + lane, m);
+    } else {  // warp w takes rows w, w + 8, ...; lanes along K
+      for (int rr = warp; rr < PK_R; rr += 8) {
+        if (r0 + rr >= R) break;
+        int m = OZ_EXP_NONE;
+        for (int kk = lane; kk < PK_K && k0 + kk < K; kk += 32) m = max(m, oz_exponent(__ldg(src + roff[rr] + koff[kk])));
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0 && m != OZ_EXP_NONE) atomicMax(exps + r0 + rr, m);
+      }
+    }
+  }
+}
+
+// The digit planes of a multi-mode operand: dst.p[s][r * Kp + k] = a_s of element (r, k),
+// zero outside the R x K operand (same strip structure as pack_kernel).
+__global__ void __launch_bounds__(256) oz_pack_kernel(const double* __restrict__ src, DevModes rm, DevModes km,
+                                                      int64_t R, int64_t K, int64_t Kp, int64_t ktiles,
+                                                      int64_t ntiles, const int* __restrict__ exps,
+                                                      PackDst dst, PackDst dst2, int r_contig) {
+  __shared__ int64_t roff[PK_R], koff[PK_K];
+  __shared__ int rexp[PK_R];
+  __shared__ double tile[PK_R][PK_K + 1];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto store = [&](int64_t o, double x, int e) {
+    int d[OZ_NS];
+    oz_digits(x, e, d);
+    __nv_bfloat16* const p[OZ_NS] = {reinterpret_cast<__nv_bfloat16*>(dst.p[0]),
+                                     reinterpret_cast<__nv_bfloat16*>(dst.p[1]),
+                                     reinterpret_cast<__nv_bfloat16*>(dst.p[2]),
+                                     reinterpret_cast<__nv_bfloat16*>(dst2.p[0]),
+                                     reinterpret_cast<__nv_bfloat16*>(dst2.p[1])};
+    float w = 1.0f;  // 2^(-7 s): the level weight of slice s (exact: |d| <= 128)
+#pragma unroll
+    for (int s = 0; s < OZ_NS; ++s, w *= 0.0078125f) p[s][o] = __float2bfloat16_rn(float(d[s]) * w);
+  };
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = (t / ktiles) * PK_R, k0 = (t % ktiles) * PK_K;
+    __syncthreads();
+    if (tid < PK_R) {
+      int64_t a = 0, c = 0;
+      if (r0 + tid < R) mode_offsets(rm, r0 + tid, a, c);
+      roff[tid] = a;
+      rexp[tid] = r0 + tid < R ? exps[r0 + tid] : OZ_EXP_NONE;
+    } else if (tid < PK_R + PK_K) {
+      const int j = tid - PK_R;
+      int64_t a = 0, c = 0;
+      if (k0 + j < K) mode_offsets(km, k0 + j, a, c);
+      koff[j] = a;
+    }
+    __syncthreads();
+    if (!r_contig) {
+#pragma unroll
+      for (int i = 0; i < PK_R / 8; ++i) {
+        const int rr = warp + 8 * i;
+        const int64_t r = r0 + rr;
+#pragma unroll
+        for (int j = 0; j < PK_K / 32; ++j) {
+          const int kk = lane + 32 * j;
+          const int64_t k = k0 + kk;
+          if (k >= Kp) continue;
+          const double v = (r < R && k < K) ? __ldg(src + roff[rr] + koff[kk]) : 0.0;
+          store(r * Kp + k, v, rexp[rr]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < PK_K / 8; ++i) {
+        const int kk = warp + 8 * i;
+        const bool ok = (r0 + lane < R) && (k0 + kk < K);
+        tile[lane][kk] = ok ? __ldg(src + roff[lane] + koff[kk]) : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < PK_R / 8; ++i) {
+        const int rr = warp + 8 * i;
+#pragma unroll
+        for (int j = 0; j < PK_K / 32; ++j) {
+          const int64_t k = k0 + lane + 32 * j;
+          if (k < Kp) store((r0 + rr) * Kp + k, tile[rr][lane + 32 * j], rexp[rr]);
+        }
+      }
+    }
+  }
+}
+
+struct OzArgs {
+  TcArgs g;           // mtiles over 128-row tiles, ntiles over OZ_BN-column tiles
+  const int* ea;      // exponent of every packed row of A
+  const int* eb;      // exponent of every packed row of B (output column)
+};
+struct OzMaps {
+  CUtensorMap a[OZ_NS], b[OZ_NS];
+};
+
+__device__ __forceinline__ Unit oz_unit_of(const TcArgs& g, int u) {
+  constexpr int GROUP_M = TATRG_GROUP_M;
+  const int tiles = g.mtiles * g.ntiles;
+  const int sidx = u / tiles, b = u - sidx * tiles;
+  const int per_group = GROUP_M * g.ntiles;
+  const int first = (b / per_group) * GROUP_M;
+  const int gsize = min(g.mtiles - first, GROUP_M);
+  const int mt = first + (b % per_group) % gsize;
+  const int nt = (b % per_group) / gsize;
+  Unit w;
+  w.m0 = int64_t(mt) * TC_BM;
+  w.n0 = int64_t(nt) * OZ_BN;
+  w.kb0 = sidx * g.kb_per_split;
+  w.nk = min(g.nkb, w.kb0 + g.kb_per_split) - w.kb0;
+  return w;
+}
+
+// Persistent kernel with the roles of tc_gemm_kernel (warp 0 TMA, one thread of warp 1
+// MMA, 16 epilogue warps); tensor memory: two buffers of three 64-column accumulators
+// (columns 0..383), running hi (384..447) and lo (448..511).
+__global__ void __maxnreg__(96) oz_gemm_kernel(const __grid_constant__ OzMaps maps, OzArgs args) {
+  constexpr int NACC = 3, ACC_COLS = NACC * OZ_BN, HI = 2 * ACC_COLS, LO = HI + OZ_BN;
+  static_assert(LO + OZ_BN == 512, "the tensor memory holds exactly 512 columns");
+  const TcArgs& g = args.g;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[OZ_STAGES], empty_bar[OZ_STAGES], acc_full[2], acc_empty[2], fin_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int64_t col_off[OZ_BN];
+  __shared__ int col_exp[OZ_BN];
+  __shared__ __align__(16) double epi_stage[EPI_WARPS * 32 * 8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int units = g.mtiles * g.ntiles * g.split;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], EPI_WARPS);
+    }
+    mbar_init(&fin_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc<1>(&tmem_base_s, 512u);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const Unit w = oz_unit_of(g, u);
+        for (int i = 0; i < w.nk; ++i, ++it) {
+          const int s = it % OZ_STAGES, round = it / OZ_STAGES;
+          if (round > 0 && !mbar_wait(&empty_bar[s], (round - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+          uint8_t* st = smem + s * OZ_STAGE;
+          mbar_expect_tx(&full_bar[s], OZ_STAGE);
+          const int kx = (w.kb0 + i) * OZ_KELEM;
+#pragma unroll
+          for (int p = 0; p < OZ_NS; ++p) {
+            tma_load_2d(st + p * OZ_A_TILE, &maps.a[p], &full_bar[s], kx, int(w.m0));
+            tma_load_2d(st + OZ_NS * OZ_A_TILE + p * OZ_B_TILE, &maps.b[p], &full_bar[s], kx, int(w.n0));
+          }
+        }
+      }
+      const uint64_t drain = now_ns() + WAIT_NS;
+      for (int i = max(0, it - OZ_STAGES); i < it; ++i) mbar_wait(&full_bar[i % OZ_STAGES], (i / OZ_STAGES) & 1, drain);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t id = idesc<2, TC_BM, OZ_BN>();
+      int it = 0, cc = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        const Unit w = oz_unit_of(g, u);
+        const int nchunks = (w.nk + OZ_KC - 1) / OZ_KC;
+        for (int c = 0; c < nchunks && ok; ++c, ++cc) {
+          const int b = cc & 1, use = cc >> 1;
+          if (use > 0 && !mbar_wait(&acc_empty[b], (use - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t acc = tmem + uint32_t(b * ACC_COLS);
+          const int i_end = min(w.nk, (c + 1) * OZ_KC);
+          for (int i = c * OZ_KC; i < i_end; ++i, ++it) {
+            const int s = it % OZ_STAGES, round = it / OZ_STAGES;
+            if (!mbar_wait(&full_bar[s], round & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t d0 = sdesc_sw64(smem_u32(smem + s * OZ_STAGE));
+            uint64_t ad[OZ_NS], bd[OZ_NS];
+#pragma unroll
+            for (int p = 0; p < OZ_NS; ++p) {
+              ad[p] = d0 + uint64_t((p * OZ_A_TILE) >> 4);
+              bd[p] = d0 + uint64_t((OZ_NS * OZ_A_TILE + p * OZ_B_TILE) >> 4);
+            }
+#pragma unroll
+            for (int kk = 0; kk < OZ_KS / 32; ++kk) {  // 16 bf16 of K per instruction
+              const uint64_t off = uint64_t(kk * 2);
+#pragma unroll
+              for (int t = 0; t < 15; ++t)
+                mma<2, 1>(acc + uint32_t(oz_acc(t) * OZ_BN), ad[oz_a(t)] + off, bd[oz_b(t)] + off, id,
+                          (i > c * OZ_KC || kk > 0 || !oz_first(t)) ? 1u : 0u);
+            }
+            mma_commit<1>(&empty_bar[s]);
+          }
+          if (ok) mma_commit<1>(&acc_full[b]);
+        }
+      }
+      mma_commit<1>(&fin_bar);
+      mbar_wait(&fin_bar, 0, now_ns() + WAIT_NS);
+    }
+  } else {
+    // epilogue warps 2..17: lane quarter q, column quarter h (16 of the 64 columns)
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    const int row = q * 32 + lane;
+    const uint32_t lanes = tmem + (uint32_t(q * 32) << 16);
+    int cc = 0;
+    bool ok = true;
+#pragma unroll 1
+    for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+      const Unit w = oz_unit_of(g, u);
+      asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+      for (int j = threadIdx.x - 64; j < OZ_BN; j += EPI_WARPS * 32) {
+        int64_t a = 0, c = 0;
+        if (w.n0 + j < g.N) mode_offsets(g.nC, w.n0 + j, a, c);
+        col_off[j] = c;
+        const int e = args.eb[w.n0 + j];
+        col_exp[j] = e == OZ_EXP_NONE ? 0 : e;
+      }
+      asm volatile("bar.sync 1, %0;" ::"r"(EPI_WARPS * 32) : "memory");
+      const int nchunks = (w.nk + OZ_KC - 1) / OZ_KC;
+#pragma unroll 1
+      for (int c = 0; c < nchunks; ++c, ++cc) {
+        const int b = cc & 1, use = cc >> 1;
+        ok = __all_sync(0xffffffffu, (ok && mbar_wait(&acc_full[b], use & 1, now_ns() + WAIT_NS)) ? 1 : 0) != 0;
+        if (!ok) break;
+        tc_fence_after();
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const uint32_t col = uint32_t(h * 16 + part * 8);
+          uint32_t v0[8], v1[8], v2[8], vh[8], vl[8];
+          tmem_ld8_nowait(lanes + uint32_t(b * ACC_COLS) + col, v0);
+          tmem_ld8_nowait(lanes + uint32_t(b * ACC_COLS + OZ_BN) + col, v1);
+          tmem_ld8_nowait(lanes + uint32_t(b * ACC_COLS + 2 * OZ_BN) + col, v2);
+          if (c > 0) {
+            tmem_ld8_nowait(lanes + uint32_t(HI) + col, vh);
+            tmem_ld8_nowait(lanes + uint32_t(LO) + col, vl);
+          }
+          tmem_wait_ld();
+          if (part == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+              asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[b])) : "memory");
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            // the chunk: level 2 (exact) + level 3 (exact) + levels 4..6, each already in
+            // units of the level-2 weight
+            const float x0 = __uint_as_float(v0[j]), x1 = __uint_as_float(v1[j]);
+            const float sum = __fadd_rn(x0, x1), bb = __fsub_rn(sum, x0);
+            float err = __fadd_rn(__fsub_rn(x0, __fsub_rn(sum, bb)), __fsub_rn(x1, bb));
+            err = __fadd_rn(err, __uint_as_float(v2[j]));
+            if (c == 0) {
+              vh[j] = __float_as_uint(sum);
+              vl[j] = __float_as_uint(err);
+            } else {
+              const float hi = __uint_as_float(vh[j]);
+              const float t2 = __fadd_rn(hi, sum), b2 = __fsub_rn(t2, hi);
+              const float e2 = __fadd_rn(__fsub_rn(hi, __fsub_rn(t2, b2)), __fsub_rn(sum, b2));
+              vh[j] = __float_as_uint(t2);
+              vl[j] = __float_as_uint(__fadd_rn(__uint_as_float(vl[j]), __fadd_rn(e2, err)));
+            }
+          }
+          tmem_st8(lanes + uint32_t(HI) + col, vh);
+          tmem_st8(lanes + uint32_t(LO) + col, vl);
+        }
+        tmem_wait_st();
+      }
+      ok = epilogue_all(ok);
+      if (ok) {
+        const bool in_rows = (w.m0 + row) < g.M;
+        int64_t roff = 0, dummy = 0;
+        if (in_rows) mode_offsets(g.mC, w.m0 + row, dummy, roff);
+        const int er0 = args.ea[w.m0 + row];
+        const int er = (er0 == OZ_EXP_NONE ? 0 : er0) - 14;
+        const double alpha = g.alpha, beta = g.beta;
+        const int mode = g.atomic ? 2 : (beta != 0.0 ? 1 : 0);
+        double* const stg = epi_stage + (warp - 2) * 256;
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const int cb = h * 16 + part * 8;  // tile column of the slice
+          if (w.n0 + cb >= g.N) break;
+          uint32_t vh[8], vl[8];
+          tmem_ld8_nowait(lanes + uint32_t(HI + cb), vh);
+          tmem_ld8_nowait(lanes + uint32_t(LO + cb), vl);
+          tmem_wait_ld();
+          __syncwarp();
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            double x = f2d_bits(__uint_as_float(vh[c])) + f2d_bits(__uint_as_float(vl[c]));
+            x = ldexp(x, er + col_exp[cb + c]);
+            if (alpha != 1.0) x *= alpha;
+            stg[lane * 8 + (c ^ (lane & 7))] = x;
+          }
+          __syncwarp();
+          const int c = lane & 7;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = (lane >> 3) + 4 * i;
+            const int64_t rb = __shfl_sync(0xffffffffu, roff, r);
+            const int rin = __shfl_sync(0xffffffffu, in_rows ? 1 : 0, r);
+            const double v = stg[r * 8 + (c ^ (r & 7))];
+            if (rin && w.n0 + cb + c < g.N) {
+              double* p = g.C + rb + col_off[cb + c];
+              if (mode == 2) atomicAdd(p, v);
+              else *p = (mode == 1) ? fma(beta, *p, v) : v;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc<1>(tmem, 512u);
+  }
 }
 
 // Shared-memory ring of the kernel: stages of the NS slices of A and of B.
@@ -1161,6 +1608,112 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
   if (st) {
     st->launches += 3 + (split > 1);
+    st->tc_launches += 1;
+    st->flops_tc += 2.0 * double(M) * double(N) * double(K);
+  }
+}
+
+void gemm_oz(const GemmDesc& d, const double* A, const double* B, double* C, cudaStream_t s, Stats* st) {
+  TATRG_CHECK(tc_available(), TATRG_ENOTIMPL, "gemm_oz: tcgen05 path needs an sm_103 GPU");
+  const int64_t M = d.m.total(), N = d.n.total(), K = d.k.total();
+  if (M == 0 || N == 0) return;
+  check_gemm(d, A, B, C);
+  const int64_t Mp = cdiv(M, TC_BM) * TC_BM, Np = cdiv(N, OZ_BN) * OZ_BN, Kp = cdiv(K, OZ_KELEM) * OZ_KELEM;
+  TATRG_CHECK(Mp < (int64_t(1) << 31) && Np < (int64_t(1) << 31), TATRG_EINVAL, "gemm_oz: operand too large");
+  // row exponents (all-zero rows keep the 0xC0 bytes) and the digit planes
+  DevBuf ex(size_t(Mp + Np) * sizeof(int), s);
+  TATRG_CUDA(cudaMemsetAsync(ex.d(), 0xC0, size_t(Mp + Np) * sizeof(int), s));
+  int* ea = ex.as<int>();
+  int* eb = ea + Mp;
+  const size_t abytes = size_t(Mp) * Kp * 2, bbytes = size_t(Np) * Kp * 2;
+  DevBuf pk(OZ_NS * (abytes + bbytes), s);
+  uint8_t* base = pk.as<uint8_t>();
+  void* pa[OZ_NS];
+  void* pb[OZ_NS];
+  for (int p = 0; p < OZ_NS; ++p) {
+    pa[p] = base + p * abytes;
+    pb[p] = base + OZ_NS * abytes + p * bbytes;
+  }
+  const int sms = sm_count();
+  auto slice = [&](const double* src, const DevModes& rm, const DevModes& km, int64_t R, int64_t Rp, int* exps,
+                   void* const* planes, int rc) {
+    const int64_t kt = cdiv(K, PK_K), nt = cdiv(R, PK_R) * kt;
+    oz_exp_kernel<<<int(std::min<int64_t>(nt, int64_t(sms) * 6)), 256, 0, s>>>(src, rm, km, R, K, kt, nt, exps, rc);
+    TATRG_CUDA(cudaGetLastError());
+    const int64_t kt2 = cdiv(Kp, PK_K), nt2 = (Rp / PK_R) * kt2;
+    PackDst d1{}, d2{};
+    d1.p[0] = planes[0];
+    d1.p[1] = planes[1];
+    d1.p[2] = planes[2];
+    d2.p[0] = planes[3];
+    d2.p[1] = planes[4];
+    oz_pack_kernel<<<int(std::min<int64_t>(nt2, int64_t(sms) * 6)), 256, 0, s>>>(src, rm, km, R, K, Kp, kt2, nt2,
+                                                                                  exps, d1, d2, rc);
+    TATRG_CUDA(cudaGetLastError());
+  };
+  {
+    DevModes rm = dev(d.m), km = dev(d.k);
+    const int rc = (d.m.n > 0 && d.m.s0[d.m.n - 1] == 1 && !(d.k.n > 0 && d.k.s0[d.k.n - 1] == 1)) ? 1 : 0;
+    slice(A, rm, km, M, Mp, ea, pa, rc);
+    DevModes rn = dev(d.n), kn = dev(d.k);
+    for (int i = 0; i < kMaxModes; ++i) kn.s0[i] = kn.s1[i];  // B's k strides
+    const int rcb = (d.n.n > 0 && d.n.s0[d.n.n - 1] == 1 && !(d.k.n > 0 && d.k.s1[d.k.n - 1] == 1)) ? 1 : 0;
+    slice(B, rn, kn, N, Np, eb, pb, rcb);
+  }
+  OzMaps maps;
+  for (int p = 0; p < OZ_NS; ++p) {
+    maps.a[p] = make_map(pa[p], Mp, Kp, 2, TC_BM, 2, OZ_KS);
+    maps.b[p] = make_map(pb[p], Np, Kp, 2, OZ_BN, 2, OZ_KS);
+  }
+  OzArgs oa;
+  TcArgs& g = oa.g;
+  g.mC = dev(d.m);
+  g.nC = dev(d.n);
+  g.M = M;
+  g.N = N;
+  g.nkb = int(Kp / OZ_KELEM);
+  g.alpha = d.alpha;
+  g.beta = d.beta;
+  g.n_contig = 0;
+  g.C = C;
+  g.mtiles = int(Mp / TC_BM);
+  g.ntiles = int(Np / OZ_BN);
+  const int64_t tiles = int64_t(g.mtiles) * g.ntiles;
+  int split = 1;
+  if (tiles < 2 * sms && g.nkb >= 8) split = int(std::min<int64_t>(cdiv(2 * sms, tiles), g.nkb / 4));
+  split = std::max(1, std::min(split, 512));
+  g.kb_per_split = int(cdiv(g.nkb, split));
+  g.split = int(cdiv(g.nkb, g.kb_per_split));
+  g.atomic = g.split > 1 ? 1 : 0;
+  oa.ea = ea;
+  oa.eb = eb;
+  if (g.split > 1) {
+    scale_c_kernel<<<int(std::min<int64_t>(cdiv(M * N, 256), 4096)), 256, 0, s>>>(C, dev(d.m), dev(d.n), M, N, d.beta);
+    TATRG_CUDA(cudaGetLastError());
+  }
+  const int64_t units = tiles * g.split;
+  TATRG_CHECK(units < (int64_t(1) << 31), TATRG_EINVAL, "gemm_oz: too many work units");
+  {
+    static std::mutex mu;
+    static std::map<int, int> fits;
+    int dev_ = 0;
+    TATRG_CUDA(cudaGetDevice(&dev_));
+    std::lock_guard<std::mutex> l(mu);
+    if (!fits.count(dev_)) {
+      TATRG_CUDA(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM));
+      int n = 0;
+      TATRG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, oz_gemm_kernel, TC_THREADS, OZ_SMEM));
+      fits[dev_] = n;
+    }
+    TATRG_CHECK(fits[dev_] >= 1, TATRG_ECUDA, "gemm_oz: the kernel does not fit on an SM");
+  }
+  const bool timed = st && st->timing;
+  if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
+  oz_gemm_kernel<<<unsigned(std::min<int64_t>(units, sms)), TC_THREADS, OZ_SMEM, s>>>(maps, oa);
+  TATRG_CUDA(cudaGetLastError());
+  if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
+  if (st) {
+    st->launches += 5 + (g.split > 1);
     st->tc_launches += 1;
     st->flops_tc += 2.0 * double(M) * double(N) * double(K);
   }

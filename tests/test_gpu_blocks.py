@@ -212,11 +212,13 @@ def _tc_case(torch, prec, M, N, K, mmodes, nmodes, kmodes, A, B, want, beta_C=No
 
 
 # relative error bound of the split products: 3xTF32 keeps 22 mantissa bits per operand and
-# accumulates in FP32; the two-term BF16 split keeps 16, the three-term one 24
-TC_TOL = {tg.TF32X3: 5e-6, tg.BF16X3: 1e-4, tg.BF16X6: 5e-6}
+# accumulates in FP32; the two-term BF16 split keeps 16, the three-term one 24.  The Ozaki
+# slices keep 36 bits of each entry relative to its row's (column's) largest, sum exactly,
+# and round the lowest levels at ~2^-34 of sum |a||b|: ~2^-32 sqrt(K) relative to max |C|
+TC_TOL = {tg.TF32X3: 5e-6, tg.BF16X3: 1e-4, tg.BF16X6: 5e-6, tg.OZAKI: 1e-8}
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 def test_contract_tensor_core_plain(torch, prec):
     rng = np.random.default_rng(11)
     M, N, K = 1000, 300, 517
@@ -226,7 +228,7 @@ def test_contract_tensor_core_plain(torch, prec):
     assert err < TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 @pytest.mark.parametrize("M,N,K", [(1037, 300, 517), (1024, 256, 4096), (2500, 130, 64), (4099, 1000, 33)])
 def test_contract_tensor_core_cta_pair_tiles(torch, prec, M, N, K):
     """M >= 1024 takes 256 x 128 tiles on CTA pairs: ragged last tile rows and columns, a
@@ -241,7 +243,7 @@ def test_contract_tensor_core_cta_pair_tiles(torch, prec, M, N, K):
     assert err < TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 def test_contract_tensor_core_cta_pair_multimode(torch, prec):
     """Permuted multi-mode operands and output on the CTA-pair path (M = 37 * 41 >= 1024)."""
     rng = np.random.default_rng(14)
@@ -256,7 +258,7 @@ def test_contract_tensor_core_cta_pair_multimode(torch, prec):
     assert err < TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 def test_contract_tensor_core_multimode_beta(torch, prec):
     """Strided (permuted) operands and output, alpha/beta, ragged tiles in M, N and K."""
     rng = np.random.default_rng(12)
@@ -272,7 +274,7 @@ def test_contract_tensor_core_multimode_beta(torch, prec):
     assert err < TC_TOL[prec], err
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 def test_contract_tensor_core_split_k_gram(torch, prec):
     """A Gram Y^T Y with a long K split across CTAs (float64 atomic reduction)."""
     rng = np.random.default_rng(13)

@@ -16,7 +16,7 @@ D0 = Da = Ds = Dg = Ks = 48
 KA = KX = 144
 Kg = 48 * 48
 NS = 2000
-TOL = {tg.TF32X3: 5e-6, tg.BF16X3: 1e-4, tg.BF16X6: 5e-6}  # as for the small contraction tests
+TOL = {tg.TF32X3: 5e-6, tg.BF16X3: 1e-4, tg.BF16X6: 5e-6, tg.OZAKI: 1e-8}  # as for the small contraction tests
 
 
 @pytest.fixture(scope="module")
@@ -30,7 +30,7 @@ def _err(got, want):
     return np.max(np.abs(got - want)) / np.max(np.abs(want))
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 def test_c2_full_shape_sampled(torch, prec):
     """C2: q[i0,kA,k,kX,g] = sum_{a,b} em[i0,kA,a,b,k] F[a,kX,b,g];
     M = 331776, N = 6912, K = 2304 (18 GB float64 output)."""
@@ -58,7 +58,7 @@ def test_c2_full_shape_sampled(torch, prec):
     assert _err(got, want) < TOL[prec], _err(got, want)
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 def test_c4_full_shape_sampled(torch, prec):
     """C4: out[i0,kG,k,g] = sum_{kA,kX} q[i0,kA,k,kX,g] P[kA,kX,kG];
     M = 110592, N = 2304, K = 20736 (the 18 GB intermediate q as operand)."""

@@ -230,3 +230,35 @@ def test_order_parameter_matches_oracle_and_sweep():
         assert abs(z[i] - r.lnz()) < 1e-11 * abs(r.lnz())
         assert abs(x[i] - trg.order_parameter_x(r.A, r.s, r.B, 3)[0]) < 1e-9 * x[i]
     assert x[2] > 1.5 > x[0]  # ordered at beta = 0.2, disordered at 0.12 (4D: beta_c ~ 0.1497)
+
+
+def test_precision_schedule_from_step_5_within_1e8():
+    """chi = 24, 40 steps: FP64 for steps 1-4 (small, cheap), the float64-grade Ozaki slices
+    for steps 5-12 (where step k still weighs 2^-k), 3xTF32 from step 13: ln Z / V within
+    1e-8 relative of the FP64 oracle."""
+    g = _gold("c2_chi24")
+    c = g["config"]
+    ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"], precision=tg.TF32X3, split_from_step=5,
+                     early_precision=tg.OZAKI, late_from_step=13).init_ising(c["beta"], c["h"], c["d"])
+    lnz = ctx.rg_step(c["steps"]).lnZ()
+    print("schedule fp64/ozaki/tf32x3: rel %.3e" % (abs(lnz - g["lnz"]) / abs(g["lnz"])))
+    assert abs(lnz - g["lnz"]) < 1e-8 * abs(g["lnz"]), (lnz, g["lnz"])
+
+
+def test_ozaki_whole_run_tracks_the_oracle():
+    """chi = 24, 40 steps with the Ozaki slices from step 1: every ln c_k of the first 20
+    steps within 1e-9 relative of the oracle's, ln Z / V within 1e-9."""
+    g = _gold("c2_chi24")
+    c = g["config"]
+    ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"], precision=tg.OZAKI,
+                     split_from_step=1).init_ising(c["beta"], c["h"], c["d"])
+    worst = 0.0
+    for k in range(c["steps"]):
+        ctx.rg_step()
+        if k < 20:
+            worst = max(worst, abs(ctx.step_info().lnc - g["lnc"][k + 1]) / max(1.0, abs(g["lnc"][k + 1])))
+    lnz = ctx.lnZ()
+    rel = abs(lnz - g["lnz"]) / abs(g["lnz"])
+    print("ozaki from step 1: rel ln Z %.3e, worst ln c_k (steps 1-20) %.3e" % (rel, worst))
+    assert worst < 1e-9 and rel < 1e-9
+

@@ -62,7 +62,7 @@ def _case(name):
 
 
 # split-precision bounds per step (measured differences are printed by the test)
-SPLIT_TOL = {tg.TF32X3: (1e-5, 1e-4), tg.BF16X3: (1e-5, 1e-4), tg.BF16X6: (1e-5, 1e-4)}
+SPLIT_TOL = {tg.TF32X3: (1e-5, 1e-4), tg.BF16X3: (1e-5, 1e-4), tg.BF16X6: (1e-5, 1e-4), tg.OZAKI: (1e-9, 1e-8)}
 
 
 @pytest.mark.parametrize("name", ["step_chi24_k20", "step_chi24_k30", "step_chi24_k39", "step_chi48_k10"])
@@ -88,7 +88,7 @@ def test_teacher_forced_step_fp64(name):
     assert np.max(np.abs(B1.ravel()[g["idx_B"]] - np.array(g["val_B"]))) < 1e-9
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6])
+@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 @pytest.mark.parametrize("name", ["step_chi24_k20", "step_chi48_k10"])
 def test_teacher_forced_step_split(name, prec):
     g, A, s, B, p, k = _case(name)
