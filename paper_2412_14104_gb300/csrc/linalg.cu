@@ -833,7 +833,15 @@ void jacobi_svd_noalloc(const double* A, int64_t m, int n, double* U, double* S,
 // are graded, so the Jacobi sweeps on R^T converge in a few sweeps where the Jacobi on A
 // takes tens.  Factoring A^T keeps the conventions of jacobi_svd: V is a full orthonormal
 // basis and the columns of U that belong to zero singular values are zero.
-bool qrcp_svd_fits(int64_t m, int n) { return n >= 32 && n <= kQrcpMaxN && m == n; }
+bool qrcp_svd_fits(int64_t m, int n) {
+  // measured on the chi = 48 step, the pivoted QR (one block) costs more than the Jacobi
+  // sweeps it saves on the step's spectra, so it is used only when TATRG_SVD_QRCP=1
+  static const bool on = []() {
+    const char* e = getenv("TATRG_SVD_QRCP");
+    return e && e[0] == '1';
+  }();
+  return on && n >= 32 && n <= kQrcpMaxN && m == n;
+}
 
 void jacobi_svd_qrcp(const double* A, int64_t m, int n, double* U, double* S, double* V, int* status_dev,
                      cudaStream_t s, Stats* st) {

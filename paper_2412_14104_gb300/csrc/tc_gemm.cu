@@ -1412,7 +1412,7 @@ namespace {
 // on the real operands, timed with CUDA events; the fastest is kept for that shape.  Each
 // candidate computes the whole result, so the output of the last one stands.  Smaller
 // contractions, and shapes not yet tuned whose output is accumulated into, take the
-// heuristic with pairs where allowed.  TATRG_AUTOTUNE=0 turns tuning off.
+// heuristic on single CTAs.  TATRG_AUTOTUNE=0 turns tuning off.
 struct TcChoice {
   bool pair = false;
   int split = 1;
@@ -1437,9 +1437,9 @@ TcChoice tuned_choice(int prec, int64_t M, int64_t N, int64_t K, int n_contig, b
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
   }
-  TcChoice def;
-  def.pair = pair_ok;
-  def.split = heuristic(pair_ok);
+  TcChoice def;  // untuned: single CTAs (on this GPU the tuner has preferred them for every shape)
+  def.pair = false;
+  def.split = heuristic(false);
   if (!on || !may_tune || 2.0 * double(M) * double(N) * double(K) < kTuneFlops) return def;
   std::vector<TcChoice> cand;
   for (int p = 0; p <= (pair_ok ? 1 : 0); ++p) {
