@@ -13,8 +13,16 @@ their own sketch keys: the path has no data exchange, so scaling is weak).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded sample of the
-same workload (one sketch application of the chi = 48 bond swap), scaled to RG steps/s by
-the step's algorithmic flop count.
+same workload (products of the chi = 48 bond-swap operator with 8 sketch columns), scaled
+to RG steps/s by the step's algorithmic flop count.
+
+Whole-run measurements of the other configurations (each writes a file under profiles/
+that the benchmark line then reports, marked as stored):
+  --c3-run       the 40-step chi = 48 run in FP64 and in split-precision schedules
+  --c4-run       the 64-temperature sweep at chi = 32 with the order parameter X^(m)
+  --c5-run       the derivatives at chi = 32 against central differences
+  --methods-run  Triad-ATRG against plain ATRG (r = 7): step time and ln Z per chi
+  --d3-run       3D Ising runs at the critical coupling
 """
 import argparse
 import json
