@@ -446,41 +446,51 @@ C5_FILE = os.path.join(ROOT, "profiles", "c5_grad_chi32.json")
 
 def run_c5(args):
     """The derivative configuration: chi = 32, r = 2, q = 2, 32 steps, beta = 0.1497,
-    h in {0, 1e-3}, seed 4.  The forward-mode derivatives of tatrg_grad (dlnZ/dbeta,
-    dlnZ/dh, d2lnZ/dbeta2 per site) against central differences of the GPU's own FP64
-    ln Z / V: step 1e-5 for the first derivatives, step 1e-4 for the second.  Writes
-    profiles/c5_grad_chi32.json; prints one JSON line."""
+    h = 1e-3 (h = 0 too with --c5-h 0,1e-3), seed 4.  The forward-mode derivatives of
+    tatrg_grad (dlnZ/dbeta, dlnZ/dh, d2lnZ/dbeta2 per site) against central differences of
+    the GPU's own FP64 ln Z / V: step 1e-5 for the first derivatives, 1e-4 for the second.
+    The difference runs are independent and run on concurrent threads and streams.  Writes
+    profiles/c5_grad_chi32.json; prints one JSON line per h."""
+    import concurrent.futures as cf
     import torch
     import paper_2412_14104_gb300 as tg
     torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
     chi, r, steps, seed, beta = 32, 2, 32, 4, 0.1497
 
     def lnz(b, h):
-        return tg.Context(chi, r, Q, seed=seed, stream=stream).init_ising(b, h, 4).rg_step(steps).lnZ()
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            z = tg.Context(chi, r, Q, seed=seed, stream=st).init_ising(b, h, 4).rg_step(steps).lnZ()
+        return z
 
     out = {}
-    for h in (0.0, 1e-3):
+    for h in [float(x) for x in args.c5_h.split(",")]:
         t0 = time.perf_counter()
-        ctx = tg.Context(chi, r, Q, seed=seed, stream=stream).init_ising(beta, h, 4).rg_step(steps)
+        e1, e2 = 1e-5, 1e-4
+        pts = [(beta + d, h) for d in (-e2, -e1, e1, e2)] + [(beta, h)]
+        if h != 0.0:
+            pts += [(beta, h + e1), (beta, h - e1)]
+        with cf.ThreadPoolExecutor(max_workers=4) as ex:
+            zs = dict(zip(pts, ex.map(lambda bh: lnz(*bh), pts)))
+        t_fd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ctx = tg.Context(chi, r, Q, seed=seed).init_ising(beta, h, 4).rg_step(steps)
         z0 = ctx.lnZ()
         gb, gh, c2 = ctx.grad(second=True)
         t_grad = time.perf_counter() - t0
-        e1, e2 = 1e-5, 1e-4
-        zb = {d: lnz(beta + d, h) for d in (-e2, -e1, e1, e2)}
-        fd_b = (zb[e1] - zb[-e1]) / (2 * e1)
-        fd_c = (zb[e2] - 2 * z0 + zb[-e2]) / (e2 * e2)
-        row = {"lnz": z0, "dlnz_dbeta": gb, "fd_dlnz_dbeta": fd_b,
-               "rel_dbeta": abs(gb - fd_b) / abs(fd_b),
+        fd_b = (zs[(beta + e1, h)] - zs[(beta - e1, h)]) / (2 * e1)
+        fd_c = (zs[(beta + e2, h)] - 2 * zs[(beta, h)] + zs[(beta - e2, h)]) / (e2 * e2)
+        row = {"lnz": z0, "lnz_repeat_rel": abs(z0 - zs[(beta, h)]) / abs(z0),
+               "dlnz_dbeta": gb, "fd_dlnz_dbeta": fd_b, "rel_dbeta": abs(gb - fd_b) / abs(fd_b),
                "d2lnz_dbeta2": c2, "fd_d2lnz_dbeta2": fd_c, "rel_d2beta": abs(c2 - fd_c) / abs(fd_c),
-               "grad_s": t_grad}
+               "grad_s": t_grad, "fd_runs_s": t_fd}
         if h != 0.0:
-            fd_h = (lnz(beta, h + e1) - lnz(beta, h - e1)) / (2 * e1)
+            fd_h = (zs[(beta, h + e1)] - zs[(beta, h - e1)]) / (2 * e1)
             row.update({"dlnz_dh": gh, "fd_dlnz_dh": fd_h, "rel_dh": abs(gh - fd_h) / abs(fd_h)})
         out["h=%g" % h] = row
         print(json.dumps({"h": h, **row}), flush=True)
     doc = {"config": "chi=32 r=2 q=2, 32 steps, beta=0.1497, seed 4, d=4, FP64",
-           "command": "python bench.py --c5-run",
+           "command": "python bench.py --c5-run --c5-h " + args.c5_h,
            "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "results": out}
     os.makedirs(os.path.dirname(C5_FILE), exist_ok=True)
     with open(C5_FILE, "w") as f:
@@ -763,6 +773,7 @@ def main():
     ap.add_argument("--methods-steps", type=int, default=24)
     ap.add_argument("--c5-run", action="store_true",
                     help="derivatives at chi = 32, 32 steps against central differences")
+    ap.add_argument("--c5-h", default="1e-3")
     ap.add_argument("--c4-run", action="store_true", help="the 64-temperature sweep at chi = 32")
     ap.add_argument("--sweep-workers", type=int, default=8)
     ap.add_argument("--c4-serial", type=int, default=16,

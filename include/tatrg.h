@@ -280,6 +280,15 @@ tatrg_status tatrg_philox_words(unsigned long long seed, uint32_t stream_id, uin
  * change the bounded waits of the tensor-core pipeline.  EINVAL for a negative limit. */
 tatrg_status tatrg_set_barrier_limit_ns(long long limit_ns);
 
+/* Launch policy of the split-precision tensor-core contractions (3xTF32, BF16x3, BF16x6;
+ * the contractions of Eqs. 1-7) for the whole process: 0 (the default) lets the autotuner
+ * pick single CTAs (128 x 128 output tiles) or CTA pairs (256 x 128 tiles on two SMs) per
+ * contraction shape, with single CTAs for untuned shapes; 1 takes CTA pairs wherever they
+ * apply (M >= 1024 output rows); -1 never takes them.  Results agree to the split form's
+ * rounding either way.  The paper has no counterpart: the setter exists so that tests and
+ * measurements can choose the tile form.  EINVAL for any other value. */
+tatrg_status tatrg_set_cta_pairs(int mode);
+
 #ifdef __cplusplus
 }
 #endif

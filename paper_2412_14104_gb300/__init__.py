@@ -82,6 +82,7 @@ def lib():
             "tatrg_svd_noalloc": [I64, I64, P, P, P, P, P],
             "tatrg_philox_words": [U64, U32, U32, U64, I64, P, P],
             "tatrg_set_barrier_limit_ns": [ctypes.c_longlong],
+            "tatrg_set_cta_pairs": [I],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -290,6 +291,12 @@ def philox_words(seed, stream_id, first, npairs, out, replica=0, stream=None):
 def set_barrier_limit_ns(limit_ns):
     """Time limit of the cooperative Jacobi SVD's grid-barrier waits on the current device."""
     _check(lib().tatrg_set_barrier_limit_ns(int(limit_ns)))
+
+
+def set_cta_pairs(mode):
+    """Tile form of the split-precision contractions: 0 autotuned, 1 CTA pairs wherever they
+    apply (M >= 1024), -1 single CTAs only."""
+    _check(lib().tatrg_set_cta_pairs(int(mode)))
 
 
 def lnz_function(chi, r, q=2, method=TRIAD, precision=FP64, seed=0, d=4, nsteps=8):

@@ -102,6 +102,9 @@ void set_barrier_limit_ns(unsigned long long ns);
 bool tc_available();
 // reads (and optionally clears) the flag a timed-out tensor-core wait raises
 int tc_error_flag(bool reset);
+// CTA-pair launch policy of the split-precision GEMM: 0 autotuned, 1 pairs wherever they
+// apply (M >= 1024), -1 never
+void set_pair_mode(int mode);
 // A Gaussian sketch operand that is generated while packing instead of read from memory
 // (the element index is the operand offset the modes give).
 struct GaussSrc {

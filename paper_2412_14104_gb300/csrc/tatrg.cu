@@ -1782,4 +1782,11 @@ tatrg_status tatrg_set_barrier_limit_ns(long long limit_ns) {
   });
 }
 
+tatrg_status tatrg_set_cta_pairs(int mode) {
+  return guard(nullptr, [&] {
+    TATRG_CHECK(mode >= -1 && mode <= 1, TATRG_EINVAL, "tatrg_set_cta_pairs: mode must be -1, 0 or 1");
+    set_pair_mode(mode);
+  });
+}
+
 }  // extern "C"
