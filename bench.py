@@ -253,10 +253,12 @@ def delta_f_check(tg):
     out = {"config": "chi=24 r=2 q=2 beta=0.1497 h=0 seed 1, 40 steps", "oracle_lnz": gold["lnz"]}
     fp = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"]).init_ising(c["beta"], c["h"], c["d"])
     out["fp64_gpu_rel"] = abs(fp.rg_step(c["steps"]).lnZ() - gold["lnz"]) / abs(gold["lnz"])
-    for s0 in (1, 11):
-        ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"], precision=tg.TF32X3,
-                         split_from_step=s0).init_ising(c["beta"], c["h"], c["d"])
-        out["tf32x3_from_step_%d_rel" % s0] = abs(ctx.rg_step(c["steps"]).lnZ() - gold["lnz"]) / abs(gold["lnz"])
+    # 3xTF32 in every step, and the schedule FP64 steps 1-4, Ozaki slices 5-12, 3xTF32 after
+    for tag, s0, early, late in (("tf32x3_from_step_1_rel", 1, 0, 0),
+                                 ("tf32x3@5/ozaki:13_rel", 5, tg.OZAKI, 13)):
+        ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"], precision=tg.TF32X3, split_from_step=s0,
+                         early_precision=early, late_from_step=late).init_ising(c["beta"], c["h"], c["d"])
+        out[tag] = abs(ctx.rg_step(c["steps"]).lnZ() - gold["lnz"]) / abs(gold["lnz"])
     return out
 
 
@@ -399,8 +401,14 @@ def run_methods(args):
     chis = [int(c) for c in args.methods_chis.split(",")]
     r = 7
     rows = {}
+    skipped = {}
     for method, mname in ((tg.TRIAD, "triad"), (tg.ATRG, "atrg")):
         for chi in chis:
+            # ATRG as the triad with identity isometries (k = chi^2) holds the squeezer
+            # environment of k^4 = chi^8 doubles: runs whose environment exceeds 100 GB are skipped
+            if method == tg.ATRG and 8.0 * chi ** 8 > 100e9:
+                skipped["atrg_%d" % chi] = "squeezer environment of 8 chi^8 = %.0f GB" % (8.0 * chi ** 8 / 1e9)
+                continue
             ctx = tg.Context(chi, r, Q, method=method, seed=SEED, precision=prec, stream=stream)
             ctx.init_ising(BETA, 0.0, 4)
             k = 0
@@ -429,12 +437,12 @@ def run_methods(args):
             x, y = np.array(pts).T
             fits[mname] = float(np.polyfit(x, y, 1)[0])
     dev = {str(c): abs(rows["triad_%d" % c]["lnz"] - rows["atrg_%d" % c]["lnz"]) / abs(rows["atrg_%d" % c]["lnz"])
-           for c in chis}
+           for c in chis if "triad_%d" % c in rows and "atrg_%d" % c in rows}
     doc = {"config": "4D Ising, beta=0.1497 h=0, r=7, q=2, seed 2, precision %s" % args.precision,
            "command": "python bench.py --methods-run --methods-chis %s --steps %d --methods-steps %d --precision %s"
                       % (args.methods_chis, args.steps, args.methods_steps, args.precision),
            "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
-           "time_exponent": fits, "triad_vs_atrg_rel_lnz": dev, "runs": rows}
+           "time_exponent": fits, "triad_vs_atrg_rel_lnz": dev, "runs": rows, "skipped": skipped}
     os.makedirs(os.path.dirname(METHODS_FILE), exist_ok=True)
     with open(METHODS_FILE, "w") as f:
         json.dump(doc, f, indent=1)
@@ -446,11 +454,12 @@ C5_FILE = os.path.join(ROOT, "profiles", "c5_grad_chi32.json")
 
 def run_c5(args):
     """The derivative configuration: chi = 32, r = 2, q = 2, 32 steps, beta = 0.1497,
-    h = 1e-3 (h = 0 too with --c5-h 0,1e-3), seed 4.  The forward-mode derivatives of
-    tatrg_grad (dlnZ/dbeta, dlnZ/dh, d2lnZ/dbeta2 per site) against central differences of
-    the GPU's own FP64 ln Z / V: step 1e-5 for the first derivatives, 1e-4 for the second.
-    The difference runs are independent and run on concurrent threads and streams.  Writes
-    profiles/c5_grad_chi32.json; prints one JSON line per h."""
+    h in --c5-h (comma separated; default 1e-3), seed 4.  The forward-mode derivatives of
+    tatrg_grad (dlnZ/dbeta, dlnZ/dh, d2lnZ/dbeta2 per site; its tangent passes run
+    concurrently) against central differences of the GPU's own FP64 ln Z / V: step 1e-5 for
+    the first derivatives, 1e-4 for the second (whose centre value is the run the derivatives
+    are taken of).  The difference runs are independent and run on concurrent threads and
+    streams.  Writes profiles/c5_grad_chi32.json after each h; prints one JSON line per h."""
     import concurrent.futures as cf
     import torch
     import paper_2412_14104_gb300 as tg
@@ -459,42 +468,48 @@ def run_c5(args):
 
     def lnz(b, h):
         st = torch.cuda.Stream()
+        t0 = time.perf_counter()
         with torch.cuda.stream(st):
             z = tg.Context(chi, r, Q, seed=seed, stream=st).init_ising(b, h, 4).rg_step(steps).lnZ()
+        print("  run beta=%.6f h=%g: lnZ/V %.16f (%.0f s)" % (b, h, z, time.perf_counter() - t0), flush=True)
         return z
 
     out = {}
     for h in [float(x) for x in args.c5_h.split(",")]:
         t0 = time.perf_counter()
-        e1, e2 = 1e-5, 1e-4
-        pts = [(beta + d, h) for d in (-e2, -e1, e1, e2)] + [(beta, h)]
-        if h != 0.0:
-            pts += [(beta, h + e1), (beta, h - e1)]
-        with cf.ThreadPoolExecutor(max_workers=4) as ex:
-            zs = dict(zip(pts, ex.map(lambda bh: lnz(*bh), pts)))
-        t_fd = time.perf_counter() - t0
-        t0 = time.perf_counter()
         ctx = tg.Context(chi, r, Q, seed=seed).init_ising(beta, h, 4).rg_step(steps)
         z0 = ctx.lnZ()
+        t_run = time.perf_counter() - t0
+        print("  run beta=%.6f h=%g: lnZ/V %.16f (%.0f s)" % (beta, h, z0, t_run), flush=True)
+        t0 = time.perf_counter()
         gb, gh, c2 = ctx.grad(second=True)
         t_grad = time.perf_counter() - t0
+        print("  tangents: %.12g %.12g %.12g (%.0f s)" % (gb, gh, c2, t_grad), flush=True)
+        e1, e2 = 1e-5, 1e-4
+        pts = [(beta + d, h) for d in (-e2, -e1, e1, e2)]
+        if h != 0.0:
+            pts += [(beta, h + e1), (beta, h - e1)]
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=3) as ex:
+            zs = dict(zip(pts, ex.map(lambda bh: lnz(*bh), pts)))
+        t_fd = time.perf_counter() - t0
         fd_b = (zs[(beta + e1, h)] - zs[(beta - e1, h)]) / (2 * e1)
-        fd_c = (zs[(beta + e2, h)] - 2 * zs[(beta, h)] + zs[(beta - e2, h)]) / (e2 * e2)
-        row = {"lnz": z0, "lnz_repeat_rel": abs(z0 - zs[(beta, h)]) / abs(z0),
+        fd_c = (zs[(beta + e2, h)] - 2 * z0 + zs[(beta - e2, h)]) / (e2 * e2)
+        row = {"lnz": z0, "run_s": t_run,
                "dlnz_dbeta": gb, "fd_dlnz_dbeta": fd_b, "rel_dbeta": abs(gb - fd_b) / abs(fd_b),
                "d2lnz_dbeta2": c2, "fd_d2lnz_dbeta2": fd_c, "rel_d2beta": abs(c2 - fd_c) / abs(fd_c),
-               "grad_s": t_grad, "fd_runs_s": t_fd}
+               "grad_s": t_grad, "fd_runs_s": t_fd, "fd_runs": len(pts)}
         if h != 0.0:
             fd_h = (zs[(beta, h + e1)] - zs[(beta, h - e1)]) / (2 * e1)
             row.update({"dlnz_dh": gh, "fd_dlnz_dh": fd_h, "rel_dh": abs(gh - fd_h) / abs(fd_h)})
         out["h=%g" % h] = row
         print(json.dumps({"h": h, **row}), flush=True)
-    doc = {"config": "chi=32 r=2 q=2, 32 steps, beta=0.1497, seed 4, d=4, FP64",
-           "command": "python bench.py --c5-run --c5-h " + args.c5_h,
-           "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "results": out}
-    os.makedirs(os.path.dirname(C5_FILE), exist_ok=True)
-    with open(C5_FILE, "w") as f:
-        json.dump(doc, f, indent=1)
+        doc = {"config": "chi=32 r=2 q=2, 32 steps, beta=0.1497, seed 4, d=4, FP64",
+               "command": "python bench.py --c5-run --c5-h " + args.c5_h,
+               "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "results": out}
+        os.makedirs(os.path.dirname(C5_FILE), exist_ok=True)
+        with open(C5_FILE, "w") as f:
+            json.dump(doc, f, indent=1)
 
 
 C4_FILE = os.path.join(ROOT, "profiles", "c4_sweep_chi32.json")
@@ -503,10 +518,11 @@ C4_FILE = os.path.join(ROOT, "profiles", "c4_sweep_chi32.json")
 def run_c4(args):
     """The temperature-sweep configuration: 64 temperatures uniformly spaced in
     beta in [0.145, 0.155], h = 0, chi = 32, r = 2, q = 2, 32 steps each, split precision
-    (3xTF32), seed 3.  Times tatrg_sweep_observables (the runs on concurrent workers) against
-    the same 64 runs one after another, and reads the order parameter X^(m) of every run to
-    locate the transition (X crosses 1.5 between the disordered value 1 and the ordered
-    value 2).  Writes profiles/c4_sweep_chi32.json; prints one JSON line."""
+    (3xTF32), seed 3.  Times tatrg_sweep_observables with --sweep-workers concurrent runs
+    against the same call with one worker (the first --c4-serial temperatures, scaled to 64),
+    and reads the order parameter X^(m) of every run after every step: for each m, the
+    transition estimate is where X^(m) first crosses 1.5 between the disordered value 1 and
+    the ordered value 2.  Writes profiles/c4_sweep_chi32.json; prints one JSON line."""
     import numpy as np
     import torch
     import paper_2412_14104_gb300 as tg
@@ -522,36 +538,39 @@ def run_c4(args):
     z, x = ctx.sweep_observables(betas, 0.0, 4, steps)
     torch.cuda.synchronize()
     t_sweep = time.perf_counter() - t0
+    one = tg.Context(chi, r, Q, seed=seed, precision=prec, sweep_workers=1, stream=stream)
+    ns = max(1, min(len(betas), args.c4_serial))
     t0 = time.perf_counter()
-    z1 = []
-    for i, b in enumerate(betas[:args.c4_serial]):
-        c = tg.Context(chi, r, Q, seed=seed, precision=prec, stream=stream)
-        c.init_ising(float(b), 0.0, 4).rg_step(steps)
-        z1.append(c.lnZ())
-        c.close()
+    z1, x1 = one.sweep_observables(betas[:ns], 0.0, 4, steps)
     torch.cuda.synchronize()
-    t_serial = (time.perf_counter() - t0) * len(betas) / max(1, args.c4_serial)
-    cross = None
-    for i in range(len(betas) - 1):
-        if (x[i] - 1.5) * (x[i + 1] - 1.5) <= 0 and x[i] != x[i + 1]:
-            cross = float(betas[i] + (1.5 - x[i]) * (betas[i + 1] - betas[i]) / (x[i + 1] - x[i]))
-            break
+    t_serial = (time.perf_counter() - t0) * len(betas) / ns
+
+    def crossing(col):
+        for i in range(len(betas) - 1):
+            if col[i] < 1.5 <= col[i + 1]:
+                return float(betas[i] + (1.5 - col[i]) * (betas[i + 1] - betas[i]) / (col[i + 1] - col[i]))
+        return None
+
+    beta_c = [crossing(x[:, m]) for m in range(steps)]
     doc = {"config": "64 beta in [0.145, 0.155], h=0, chi=32 r=2 q=2, 32 steps, %s, seed 3, %d workers"
                      % (args.precision, args.sweep_workers),
            "command": "python bench.py --c4-run --sweep-workers %d --c4-serial %d --precision %s"
                       % (args.sweep_workers, args.c4_serial, args.precision),
            "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
            "sweep_s": t_sweep, "serial_s_for_64": t_serial,
-           "serial_note": "the first %d runs one after another, scaled to 64" % args.c4_serial,
+           "serial_note": "the first %d temperatures through the same call with one worker, scaled to 64" % ns,
            "runs_per_s_sweep": len(betas) / t_sweep, "runs_per_s_serial": len(betas) / t_serial,
            "rg_steps_per_s_sweep": len(betas) * steps / t_sweep,
-           "serial_matches_sweep": [abs(a - b) / abs(b) for a, b in zip(z1, z[:len(z1)])],
-           "beta_c_estimate": cross, "betas": betas.tolist(), "lnz": z.tolist(), "X": x.tolist()}
+           "serial_vs_sweep_rel_lnz": [abs(a - b) / abs(b) for a, b in zip(z1, z[:ns])],
+           "beta_c_by_step": beta_c,
+           "x_max_by_step": [float(x[:, m].max()) for m in range(steps)],
+           "x_min_by_step": [float(x[:, m].min()) for m in range(steps)],
+           "betas": betas.tolist(), "lnz": z.tolist(), "X_by_step": x.tolist()}
     os.makedirs(os.path.dirname(C4_FILE), exist_ok=True)
     with open(C4_FILE, "w") as f:
         json.dump(doc, f, indent=1)
     print(json.dumps({k: doc[k] for k in ("config", "sweep_s", "serial_s_for_64", "runs_per_s_sweep",
-                                          "runs_per_s_serial", "beta_c_estimate")}), flush=True)
+                                          "runs_per_s_serial", "beta_c_by_step", "x_max_by_step")}), flush=True)
 
 
 D3_FILE = os.path.join(ROOT, "profiles", "d3_runs.json")
@@ -733,7 +752,7 @@ def run_ours(args, world, rank, local):
     stored = {}
     for name, path, keys in (
             ("c4_sweep", C4_FILE, ("config", "when", "command", "runs_per_s_sweep", "runs_per_s_serial",
-                                   "rg_steps_per_s_sweep", "beta_c_estimate")),
+                                   "rg_steps_per_s_sweep", "beta_c_by_step")),
             ("c5_grad", C5_FILE, ("config", "when", "command", "results")),
             ("methods", METHODS_FILE, ("config", "when", "command", "time_exponent", "triad_vs_atrg_rel_lnz")),
             ("d3", D3_FILE, ("config", "when", "command", "runs"))):
@@ -769,7 +788,7 @@ def main():
     ap.add_argument("--c3-forms", default="fp64,tf32x3@1,bf16x3@1,tf32x3@5,bf16x3@5,tf32x3@9,bf16x3@9,tf32x3@13,bf16x3@13")
     ap.add_argument("--methods-run", action="store_true",
                     help="Triad-ATRG against ATRG (r = 7): step time and ln Z / V per chi")
-    ap.add_argument("--methods-chis", default="8,12,16,20,24")
+    ap.add_argument("--methods-chis", default="8,12,16,18,20,24")
     ap.add_argument("--methods-steps", type=int, default=24)
     ap.add_argument("--c5-run", action="store_true",
                     help="derivatives at chi = 32, 32 steps against central differences")

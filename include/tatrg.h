@@ -118,9 +118,11 @@ tatrg_status tatrg_lnZ(tatrg_ctx* ctx, double* lnZ_per_site);
  * first derivative (two more passes).  The computed ln Z / V is piecewise smooth: where
  * kept singular values of different symmetry sectors cross, the ordered basis that later
  * sketches act on changes and ln Z / V jumps at the level of the truncation error; the
- * derivatives are those of the piece that contains (beta, h).  Needs a state made by tatrg_init_ising; any of the
- * three host pointers may be null (not all).  Runs on the context's stream, synchronises,
- * and leaves the context's state untouched.  At h = 0 the h-derivative of the algorithm
+ * derivatives are those of the piece that contains (beta, h).  Needs a state made by
+ * tatrg_init_ising; any of the three host pointers may be null (not all).  The passes are
+ * independent and run concurrently, each on its own host thread and non-blocking stream,
+ * after the work already queued on the context's stream; the call synchronises and leaves
+ * the context's state untouched.  At h = 0 the h-derivative of the algorithm
  * is not smooth where symmetry-degenerate values split; use it at h != 0. */
 tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh,
                         double* d2lnZ_dbeta2 /* nullable */);
@@ -134,9 +136,13 @@ tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh,
 tatrg_status tatrg_sweep(tatrg_ctx* ctx, const double* betas, int nbeta, double h, int d,
                          int nsteps, double* lnZ_out);
 
-/* The same temperature runs, also writing to the host array X_out (nullable) the order
- * parameter X^(m) of tatrg_order_parameter at leg position d - 1 after the last step of each
- * run: the temperature scan of Sec. 3 that locates the transition point. */
+/* The same temperature runs, also writing to the host array X_out (nullable, nbeta * nsteps
+ * doubles) the order parameter X^(m) of tatrg_order_parameter at leg position d - 1 after
+ * every step: X_out[i * nsteps + m - 1] is X^(m) of temperature i.  This is the temperature
+ * scan of Sec. 3 that locates the transition point; the whole history is returned because
+ * at h = 0 the two-fold degeneracy of the ordered phase is itself lost after enough steps
+ * (rounding breaks the Z2 symmetry and the flow amplifies it), so X^(m) of the ordered
+ * phase rises to 2 and later decays toward 1. */
 tatrg_status tatrg_sweep_observables(tatrg_ctx* ctx, const double* betas, int nbeta, double h,
                                      int d, int nsteps, double* lnZ_out, double* X_out);
 
@@ -281,12 +287,16 @@ tatrg_status tatrg_philox_words(unsigned long long seed, uint32_t stream_id, uin
 tatrg_status tatrg_set_barrier_limit_ns(long long limit_ns);
 
 /* Launch policy of the split-precision tensor-core contractions (3xTF32, BF16x3, BF16x6;
- * the contractions of Eqs. 1-7) for the whole process: 0 (the default) lets the autotuner
- * pick single CTAs (128 x 128 output tiles) or CTA pairs (256 x 128 tiles on two SMs) per
- * contraction shape, with single CTAs for untuned shapes; 1 takes CTA pairs wherever they
- * apply (M >= 1024 output rows); -1 never takes them.  Results agree to the split form's
- * rounding either way.  The paper has no counterpart: the setter exists so that tests and
- * measurements can choose the tile form.  EINVAL for any other value. */
+ * the contractions of Eqs. 1-7) for the whole process.  Tile forms: single CTAs (one
+ * 128 x 128 output tile per CTA); CTA pairs (cta_group::2: one tensor-core MMA of
+ * 256 x 128 on two SMs, each holding half of the B tile); multicast clusters (two CTAs
+ * with a 128 x 128 tile each, stacked in M, each loading half of the shared B tile and
+ * multicasting it to both).  mode 0 (the default) lets the autotuner pick the form and the
+ * split of K per contraction shape, with single CTAs for untuned shapes; 1 takes CTA pairs
+ * and 2 multicast clusters wherever they apply (M >= 1024 output rows); -1 never takes the
+ * two-CTA forms.  Results agree to the split form's rounding whatever the form.  The paper
+ * has no counterpart: the setter exists so that tests and measurements can choose the
+ * form.  EINVAL for any other value. */
 tatrg_status tatrg_set_cta_pairs(int mode);
 
 #ifdef __cplusplus

@@ -163,9 +163,10 @@ class Context:
         return out
 
     def sweep_observables(self, betas, h, d, nsteps):
-        """(ln Z / V, X^(m) at leg d - 1) of every temperature run."""
+        """(ln Z / V of every temperature run, X^(m) at leg d - 1 after every step as an
+        array of shape (len(betas), nsteps))."""
         b = np.ascontiguousarray(betas, dtype=np.float64)
-        z, x = np.empty_like(b), np.empty_like(b)
+        z, x = np.empty_like(b), np.empty((b.size, nsteps))
         _check(lib().tatrg_sweep_observables(self._h, _dptr(b), b.size, h, d, nsteps, _dptr(z),
                                              _dptr(x)), self._h)
         return z, x
@@ -294,8 +295,8 @@ def set_barrier_limit_ns(limit_ns):
 
 
 def set_cta_pairs(mode):
-    """Tile form of the split-precision contractions: 0 autotuned, 1 CTA pairs wherever they
-    apply (M >= 1024), -1 single CTAs only."""
+    """Tile form of the split-precision contractions: 0 autotuned, 1 CTA pairs, 2 multicast
+    clusters wherever they apply (M >= 1024), -1 single CTAs only."""
     _check(lib().tatrg_set_cta_pairs(int(mode)))
 
 

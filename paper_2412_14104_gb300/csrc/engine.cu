@@ -102,7 +102,7 @@ OrthResult Engine::orth(const double* Y, int64_t m, int64_t n) {
   TATRG_CHECK(n >= 1, TATRG_EINVAL, "orth: empty matrix");
   bool ok = false;
   OrthResult r;
-  if (m >= n) {
+  if (m >= n && n <= cholesky_max_n()) {
     // FP64 Grams: plain CholeskyQR2.  Split-precision Grams carry ~1e-7 relative error, so
     // their first pass is shifted (shifted CholeskyQR3).
     r = cholqr2(Y, m, n, fp64_grade() ? 0.0 : 1e-6, ok);
@@ -131,6 +131,7 @@ OrthResult Engine::orth(const double* Y, int64_t m, int64_t n) {
 
 Engine::MetricOrth Engine::orth_metric(const double* X, int64_t nin, int64_t w, const Op& metric) {
   MetricOrth out;
+  if (w > cholesky_max_n()) return out;  // ok = false: the caller takes the explicit path
   const int passes = fp64_grade() ? 2 : 3;
   const double shift = fp64_grade() ? 0.0 : 1e-6;
   DevBuf G(w * w * sizeof(double), s_), Rk(w * w * sizeof(double), s_), Ri(w * w * sizeof(double), s_),

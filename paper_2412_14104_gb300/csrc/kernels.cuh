@@ -72,6 +72,8 @@ void fill(double* x, int64_t n, double v, cudaStream_t s);
 void check_finite(const double* x, int64_t n, int* bad_dev, cudaStream_t s);
 
 // linalg.cu ---------------------------------------------------------------------------
+// largest n of the one-block Cholesky (its working matrix lives in shared memory)
+int cholesky_max_n();
 // Cholesky G = R^T R of an n x n SPD matrix (row-major); R upper (row-major, zero below).
 // *status_dev = 0 on success, 1 when a pivot is not positive relative to its diagonal.
 void cholesky(const double* G, int n, double* R, int* status_dev, double shift_rel,
@@ -102,8 +104,8 @@ void set_barrier_limit_ns(unsigned long long ns);
 bool tc_available();
 // reads (and optionally clears) the flag a timed-out tensor-core wait raises
 int tc_error_flag(bool reset);
-// CTA-pair launch policy of the split-precision GEMM: 0 autotuned, 1 pairs wherever they
-// apply (M >= 1024), -1 never
+// two-CTA tile forms of the split-precision GEMM: 0 autotuned, 1 CTA pairs, 2 multicast
+// clusters wherever they apply (M >= 1024), -1 never
 void set_pair_mode(int mode);
 // A Gaussian sketch operand that is generated while packing instead of read from memory
 // (the element index is the operand offset the modes give).

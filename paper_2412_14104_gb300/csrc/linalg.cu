@@ -10,8 +10,11 @@
 namespace tatrg {
 namespace {
 
+constexpr int kCholMaxN = 168;
+
 // Right-looking Cholesky G + shift I = R^T R with the upper triangle of the working
-// matrix in shared memory (full n x n storage, n <= 160).  Step j scales row j by the
+// matrix in shared memory (full n x n storage, n <= kCholMaxN: 168^2 doubles and the
+// kernel's own arrays fill the 227 KB a block may hold).  Step j scales row j by the
 // pivot square root, then subtracts the outer product of the scaled row from the trailing
 // block; the thread that updates the next diagonal entry takes its square root at once
 // (FP64 square roots and divisions are scarce on this GPU, so they are not repeated per
@@ -23,7 +26,7 @@ __global__ void __launch_bounds__(1024) cholesky_kernel(const double* G, int n, 
   __shared__ double shift, djj_s[2];
   __shared__ int fail_s;
   __shared__ double red[32];
-  __shared__ double ref[160];
+  __shared__ double ref[kCholMaxN];
   const int tid = threadIdx.x, nt = blockDim.x;
   const int tx = tid & 31, ty = tid >> 5;  // 32 x 32 threads over (k, i)
   {
@@ -651,13 +654,15 @@ __global__ void permute_rows_kernel(const double* Ux, const int* perm, int n, do
 bool single_block_fits(int64_t m, int N) { return N < 32 && m * N * int64_t(sizeof(double)) <= 200 * 1024; }
 }  // namespace
 
+int cholesky_max_n() { return kCholMaxN; }
+
 void cholesky(const double* G, int n, double* R, int* status_dev, double shift_rel,
               cudaStream_t s) {
   check_extent(G, int64_t(n) * n - 1, sizeof(double), "cholesky input");
   check_extent(R, int64_t(n) * n - 1, sizeof(double), "cholesky output");
-  TATRG_CHECK(n >= 1 && n <= 160, TATRG_EINVAL, "cholesky: n must be <= 160");
+  TATRG_CHECK(n >= 1 && n <= kCholMaxN, TATRG_EINVAL, "cholesky: n must be <= 168");
   const size_t sm = size_t(n) * n * sizeof(double);
-  ensure_smem_attr(reinterpret_cast<const void*>(cholesky_kernel), 160 * 160 * 8);
+  ensure_smem_attr(reinterpret_cast<const void*>(cholesky_kernel), kCholMaxN * kCholMaxN * 8);
   cholesky_kernel<<<1, 1024, sm, s>>>(G, n, R, status_dev, shift_rel);
   TATRG_CUDA(cudaGetLastError());
 }

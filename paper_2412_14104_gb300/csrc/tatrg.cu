@@ -1465,11 +1465,12 @@ tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh, dou
   return guard(ctx, [&] {
     TATRG_CHECK(ctx->ready && ctx->ising, TATRG_ESTATE, "tatrg_grad needs a run started by tatrg_init_ising");
     // One FP64 tangent pass per derivative: the same run (parameters, replica, number of
-    // steps) with the tangent of every tensor carried beside it.
-    auto tangent = [&](double beta, int dir) {
+    // steps) with the tangent of every tensor carried beside it.  The passes are
+    // independent; each runs on its own host thread and non-blocking stream.
+    auto tangent = [&](double beta, int dir, cudaStream_t s) {
       tatrg_params pp = ctx->p;
       pp.precision = TATRG_FP64;
-      tatrg_ctx sub(pp, ctx->stream);
+      tatrg_ctx sub(pp, s);
       sub.replica = ctx->replica;
       sub.tan_on = true;
       sub.tan_dir = dir;
@@ -1486,15 +1487,59 @@ tatrg_status tatrg_grad(tatrg_ctx* ctx, double* dlnZ_dbeta, double* dlnZ_dh, dou
       }
       return sum + std::ldexp(sub.trace_tan(tt), -sub.step);
     };
-    if (dlnZ_dbeta) *dlnZ_dbeta = tangent(ctx->beta0, 0);
-    if (dlnZ_dh) *dlnZ_dh = tangent(ctx->beta0, 1);
-    if (d2lnZ_dbeta2) {
-      // central difference of the exact first derivative; the computed ln Z / V is only
-      // piecewise smooth (ordered bases change where singular values of different
-      // symmetry sectors cross), so the step stays small
-      const double e = 1e-6 * std::max(1.0, ctx->beta0);
+    // second derivative: central difference of the exact first derivative; the computed
+    // ln Z / V is only piecewise smooth (ordered bases change where singular values of
+    // different symmetry sectors cross), so the step stays small
+    const double e = 1e-6 * std::max(1.0, ctx->beta0);
+    if (d2lnZ_dbeta2)
       TATRG_CHECK(ctx->beta0 - e > 0.0, TATRG_EINVAL, "tatrg_grad: beta too small for the second derivative");
-      *d2lnZ_dbeta2 = (tangent(ctx->beta0 + e, 0) - tangent(ctx->beta0 - e, 0)) / (2.0 * e);
+    struct Pass {
+      double beta;
+      int dir;
+      double out = 0.0;
+    };
+    std::vector<Pass> passes;
+    if (dlnZ_dbeta) passes.push_back({ctx->beta0, 0});
+    if (dlnZ_dh) passes.push_back({ctx->beta0, 1});
+    if (d2lnZ_dbeta2) {
+      passes.push_back({ctx->beta0 + e, 0});
+      passes.push_back({ctx->beta0 - e, 0});
+    }
+    int dev = 0;
+    TATRG_CUDA(cudaGetDevice(&dev));
+    TATRG_CUDA(cudaStreamSynchronize(ctx->stream));
+    std::mutex mu;
+    tatrg_status first = TATRG_OK;
+    std::string first_msg;
+    std::vector<std::thread> pool;
+    for (auto& ps : passes) {
+      pool.emplace_back([&, pp = &ps]() {
+        cudaStream_t s = nullptr;
+        try {
+          TATRG_CUDA(cudaSetDevice(dev));
+          TATRG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+          pp->out = tangent(pp->beta, pp->dir, s);
+        } catch (const Error& err) {
+          std::lock_guard<std::mutex> l(mu);
+          if (first == TATRG_OK) { first = err.code; first_msg = err.what(); }
+        } catch (const std::exception& err) {
+          std::lock_guard<std::mutex> l(mu);
+          if (first == TATRG_OK) { first = TATRG_ECUDA; first_msg = err.what(); }
+        }
+        if (s) {
+          cudaStreamSynchronize(s);
+          cudaStreamDestroy(s);
+        }
+      });
+    }
+    for (auto& t : pool) t.join();
+    if (first != TATRG_OK) throw Error(first, first_msg);
+    size_t i = 0;
+    if (dlnZ_dbeta) *dlnZ_dbeta = passes[i++].out;
+    if (dlnZ_dh) *dlnZ_dh = passes[i++].out;
+    if (d2lnZ_dbeta2) {
+      *d2lnZ_dbeta2 = (passes[i].out - passes[i + 1].out) / (2.0 * e);
+      i += 2;
     }
     TATRG_CHECK(tc_error_flag(true) == 0, TATRG_ETIMEOUT, "a tensor-core pipeline wait timed out");
   });
@@ -1538,11 +1583,13 @@ tatrg_status tatrg_sweep_observables(tatrg_ctx* ctx, const double* betas, int nb
             tatrg_ctx sub(ctx->p, s);
             sub.replica = uint32_t(i);
             sub.init_ising(betas[i], h, d);
-            for (int k = 0; k < nsteps; ++k) sub.rg_step();
+            for (int k = 0; k < nsteps; ++k) {
+              sub.rg_step();
+              if (X_out) X_out[int64_t(i) * nsteps + k] = sub.order_parameter(d - 1);
+            }
             double tt = sub.trace();
             TATRG_CHECK(tt > 0.0 && std::isfinite(tt), TATRG_ENUMERIC, "non-positive final trace in sweep");
             lnZ_out[i] = sub.partial_lnz() + std::ldexp(std::log(tt), -sub.step);
-            if (X_out) X_out[i] = sub.order_parameter(d - 1);
           }
         } catch (const Error& e) {
           fail(e.code, e.what());
@@ -1784,7 +1831,7 @@ tatrg_status tatrg_set_barrier_limit_ns(long long limit_ns) {
 
 tatrg_status tatrg_set_cta_pairs(int mode) {
   return guard(nullptr, [&] {
-    TATRG_CHECK(mode >= -1 && mode <= 1, TATRG_EINVAL, "tatrg_set_cta_pairs: mode must be -1, 0 or 1");
+    TATRG_CHECK(mode >= -1 && mode <= 2, TATRG_EINVAL, "tatrg_set_cta_pairs: mode must be -1, 0, 1 or 2");
     set_pair_mode(mode);
   });
 }

@@ -122,6 +122,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// the same box written to the same shared-memory offset of every CTA in `mask` (a cluster of
+// this GPU's own CTAs), each of whose barriers at `bar`'s offset receives the bytes it got
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], "
+      "[%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -182,6 +192,15 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
         "h"(uint16_t(3))
         : "memory");
   }
+}
+// completion of one CTA's MMAs issued so far arrives once on the barrier at `bar`'s offset
+// in every CTA of `mask`
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
 }
 template <int CG>
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t cols) {
@@ -386,13 +405,20 @@ struct TcMaps {
   CUtensorMap a[3], b[3];  // slice panels of A and B (the first NS are used)
 };
 
-template <int PREC, int NS, int KC, int STAGES, int NBUF, bool PAIR>
+// Tile forms: FORM 0, one CTA per 128 x 128 tile; FORM 1, CTA pairs (cta_group::2: one MMA
+// for a 256 x 128 tile, each CTA holding 128 rows of A and half of B); FORM 2, clusters of
+// two CTAs with a 128 x 128 tile each, stacked in M, sharing the B tile: each CTA loads half
+// of B's rows and multicasts them to both, so every CTA reads 3/4 of the operand bytes of
+// FORM 0 from L2 for the same output.
+template <int PREC, int NS, int KC, int STAGES, int NBUF, int FORM>
 __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's register file
     tc_gemm_kernel(const __grid_constant__ TcMaps maps, TcArgs g) {
+  constexpr bool PAIR = FORM == 1, MC = FORM == 2, CLU = FORM != 0;
   constexpr int CG = PAIR ? 2 : 1;
   constexpr int BN = TC_BN;
-  constexpr int TILE_M = TC_BM * CG;        // output rows per tile (per pair)
-  constexpr int B_ROWS = BN / CG;           // rows of B (output columns) per CTA
+  constexpr int TILE_M = CLU ? 2 * TC_BM : TC_BM;  // output rows per work unit
+  constexpr int B_ROWS = PAIR ? BN / 2 : BN;       // rows of B (output columns) in a CTA's stage
+  constexpr int B_LOAD = CLU ? BN / 2 : BN;        // rows of B a CTA loads per stage
   constexpr int A_TILE = TC_BM * KSLICE;    // bytes
   constexpr int B_TILE = B_ROWS * KSLICE;
   constexpr int STAGE = NS * (A_TILE + B_TILE);
@@ -411,14 +437,14 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int units = g.mtiles * g.ntiles * g.split;
-  const uint32_t rank = PAIR ? cluster_rank() : 0u;
-  const int first = PAIR ? int(blockIdx.x >> 1) : int(blockIdx.x);  // this CTA's (pair's) first unit
-  const int stride = PAIR ? int(gridDim.x >> 1) : int(gridDim.x);
+  const uint32_t rank = CLU ? cluster_rank() : 0u;
+  const int first = CLU ? int(blockIdx.x >> 1) : int(blockIdx.x);  // this CTA's (cluster's) first unit
+  const int stride = CLU ? int(gridDim.x >> 1) : int(gridDim.x);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+      mbar_init(&empty_bar[s], MC ? 2 : 1);  // FORM 2: both CTAs' MMAs read the stage's B
       mbar_init(&peer_full[s], 1);
     }
     for (int b = 0; b < NBUF; ++b) {
@@ -429,7 +455,7 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  if (PAIR) cluster_sync_all();  // both CTAs' barriers exist before any remote arrive
+  if (CLU) cluster_sync_all();  // both CTAs' barriers exist before any remote arrive or copy
   if (warp == 1) tmem_alloc<CG>(&tmem_base_s, uint32_t(TMEM_COLS));
   tc_fence_before();
   __syncthreads();
@@ -444,15 +470,19 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
         const Unit w = unit_of<TILE_M>(g, u);
         for (int i = 0; i < w.nk; ++i, ++it) {
           const int s = it % STAGES, round = it / STAGES;
-          if (round > 0 && !mbar_wait<PAIR>(&empty_bar[s], (round - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
+          if (round > 0 && !mbar_wait<CLU>(&empty_bar[s], (round - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
           uint8_t* st = smem + s * STAGE;
-          mbar_expect_tx(&full_bar[s], STAGE);
+          mbar_expect_tx(&full_bar[s], STAGE);  // FORM 2: half of B comes from the other CTA
           const int kx = (w.kb0 + i) * KELEM;
-          const int ya = int(w.m0) + int(rank) * TC_BM, yb = int(w.n0) + int(rank) * B_ROWS;
+          const int ya = int(w.m0) + int(rank) * TC_BM, yb = int(w.n0) + int(rank) * B_LOAD;
 #pragma unroll
           for (int p = 0; p < NS; ++p) {
             tma_load_2d(st + p * A_TILE, &maps.a[p], &full_bar[s], kx, ya);
-            tma_load_2d(st + NS * A_TILE + p * B_TILE, &maps.b[p], &full_bar[s], kx, yb);
+            if (MC)
+              tma_load_2d_mc(st + NS * A_TILE + p * B_TILE + int(rank) * B_LOAD * KSLICE, &maps.b[p], &full_bar[s],
+                             kx, yb, uint16_t(3));
+            else
+              tma_load_2d(st + NS * A_TILE + p * B_TILE, &maps.b[p], &full_bar[s], kx, yb);
           }
         }
       }
@@ -461,9 +491,9 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
       for (int i = max(0, it - STAGES); i < it; ++i)
         mbar_wait(&full_bar[i % STAGES], (i / STAGES) & 1, drain);
     }
-  } else if (warp == 1 && rank == 0) {
+  } else if (warp == 1 && (!PAIR || rank == 0)) {
     if (lane == 0) {
-      constexpr uint32_t id = idesc<PREC, TILE_M, BN>();
+      constexpr uint32_t id = idesc<PREC, PAIR ? 2 * TC_BM : TC_BM, BN>();
       int it = 0, cc = 0;  // stage uses and chunks, continued across units
       bool ok = true;
       for (int u = first; u < units && ok; u += stride) {
@@ -497,7 +527,8 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
                 mma<PREC, CG>(acc, ad[Products<NS>::a(t)] + off, bd[Products<NS>::b(t)] + off, id,
                               (i > c * KC || kk > 0 || t > 0) ? 1u : 0u);
             }
-            mma_commit<CG>(&empty_bar[s]);
+            if (MC) mma_commit_mc(&empty_bar[s], uint16_t(3));  // both CTAs wrote this stage's B
+            else mma_commit<CG>(&empty_bar[s]);
           }
           if (ok) mma_commit<CG>(&acc_full[b]);
         }
@@ -506,7 +537,7 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
       mma_commit<CG>(&fin_bar);
       mbar_wait<PAIR>(&fin_bar, 0, now_ns() + WAIT_NS);
     }
-  } else if (warp == 1) {
+  } else if (warp == 1) {  // PAIR, rank 1
     if (lane == 0) {
       // second CTA of a pair: forward "stage landed" to the first CTA, which issues the MMAs
       const uint32_t peer0 = cluster_addr(&peer_full[0], 0);
@@ -665,9 +696,9 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
   }
   tc_fence_before();
   __syncthreads();
-  // a pair: no CTA releases its tensor memory or exits while the other may still arrive on
-  // its barriers
-  if (PAIR) cluster_sync_all();
+  // a cluster: no CTA releases its tensor memory or exits while the other may still arrive
+  // on its barriers or copy into its shared memory
+  if (CLU) cluster_sync_all();
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc<CG>(tmem, uint32_t(TMEM_COLS));
@@ -1298,15 +1329,16 @@ __global__ void __maxnreg__(96) oz_gemm_kernel(const __grid_constant__ OzMaps ma
 }
 
 // Shared-memory ring of the kernel: stages of the NS slices of A and of B.
-// launch policy for CTA pairs: 0 = the autotuner decides (single CTAs untuned), 1 = pairs
+// launch policy for the two-CTA tile forms: 0 = the autotuner decides (single CTAs
+// untuned), 1 = CTA pairs (FORM 1) wherever they apply, 2 = multicast clusters (FORM 2)
 // wherever they apply, -1 = never
 std::atomic<int> g_pair_mode{0};
 
-template <int NS, bool PAIR>
-constexpr int stage_bytes() { return NS * (TC_BM * KSLICE + (PAIR ? TC_BN / 2 : TC_BN) * KSLICE); }
+template <int NS, int FORM>
+constexpr int stage_bytes() { return NS * (TC_BM * KSLICE + (FORM == 1 ? TC_BN / 2 : TC_BN) * KSLICE); }
 
-// Largest number of CTAs (of pairs: clusters) that are resident at once, per device.
-template <int PREC, int NS, bool PAIR>
+// Largest number of CTAs (of clusters) that are resident at once, per device.
+template <int PREC, int NS, int FORM>
 int resident_units(const void* kfn, int smem) {
   static std::mutex mu;
   static std::map<int, int> cache;
@@ -1317,7 +1349,7 @@ int resident_units(const void* kfn, int smem) {
   if (it != cache.end()) return it->second;
   TATRG_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int n = 0;
-  if (PAIR) {
+  if (FORM != 0) {
     TATRG_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
@@ -1341,19 +1373,19 @@ int resident_units(const void* kfn, int smem) {
   return n;
 }
 
-template <int PREC, int NS, bool PAIR>
+template <int PREC, int NS, int FORM>
 void launch(const TcMaps& maps, const TcArgs& a, int64_t units, cudaStream_t s) {
-  constexpr int STAGE = stage_bytes<NS, PAIR>();
+  constexpr int STAGE = stage_bytes<NS, FORM>();
   constexpr int STAGES = SMEM_BUDGET / STAGE;
   static_assert(STAGES >= 2, "the ring needs two stages");
   constexpr int KC_ = TATRG_CHAIN_K / (PREC == 1 ? KSLICE / 4 : KSLICE / 2);  // stages per FP32 chain
   constexpr int KC = KC_ > 0 ? KC_ : 1;  // at least one stage
   constexpr int SMEM = STAGES * STAGE + 1024;
-  auto k = tc_gemm_kernel<PREC, NS, KC, STAGES, 2, PAIR>;
-  const int resident = resident_units<PREC, NS, PAIR>(reinterpret_cast<const void*>(k), SMEM);
-  // persistent: every CTA (pair) walks units b, b + grid, ...; no more CTAs than are resident
+  auto k = tc_gemm_kernel<PREC, NS, KC, STAGES, 2, FORM>;
+  const int resident = resident_units<PREC, NS, FORM>(reinterpret_cast<const void*>(k), SMEM);
+  // persistent: every CTA (cluster) walks units b, b + grid, ...; no more than are resident
   const unsigned n = unsigned(std::min<int64_t>(units, resident));
-  if (!PAIR) {
+  if (FORM == 0) {
     k<<<n, TC_THREADS, SMEM, s>>>(maps, a);
   } else {
     cudaLaunchConfig_t cfg = {};
@@ -1373,8 +1405,8 @@ void launch(const TcMaps& maps, const TcArgs& a, int64_t units, cudaStream_t s) 
   TATRG_CUDA(cudaGetLastError());
 }
 
-// CTA pairs for the contractions with many 256-row tiles (set TATRG_CTA_PAIR=0 to use single
-// CTAs everywhere, e.g. to compare the two).
+// The two-CTA tile forms for the contractions with many 256-row tiles (set TATRG_CTA_PAIR=0
+// to use single CTAs everywhere, e.g. to compare).
 bool pairs_enabled() {
   static const bool on = []() {
     const char* e = getenv("TATRG_CTA_PAIR");
@@ -1417,13 +1449,13 @@ int tc_error_flag(bool reset) {
 namespace {
 // Autotuner of the launch configuration: the first time a large contraction of a given
 // shape is seen on a device (and its output is overwritten, beta = 0), every candidate --
-// single CTAs or CTA pairs, the split-K heuristic's factor, half and twice it -- runs once
+// each tile form, the split-K heuristic's factor, half and twice it -- runs once
 // on the real operands, timed with CUDA events; the fastest is kept for that shape.  Each
 // candidate computes the whole result, so the output of the last one stands.  Smaller
 // contractions, and shapes not yet tuned whose output is accumulated into, take the
 // heuristic on single CTAs.  TATRG_AUTOTUNE=0 turns tuning off.
 struct TcChoice {
-  bool pair = false;
+  int form = 0;  // tile form of tc_gemm_kernel
   int split = 1;
 };
 
@@ -1446,18 +1478,19 @@ TcChoice tuned_choice(int prec, int64_t M, int64_t N, int64_t K, int n_contig, b
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
   }
-  TcChoice def;  // untuned: single CTAs (on this GPU the tuner has preferred them for every shape)
-  def.pair = false;
+  TcChoice def;  // untuned: single CTAs
+  def.form = 0;
   def.split = heuristic(false);
-  if (pair_ok && g_pair_mode.load() == 1) return TcChoice{true, heuristic(true)};
+  const int mode = g_pair_mode.load();
+  if (pair_ok && (mode == 1 || mode == 2)) return TcChoice{mode, heuristic(true)};
   if (!on || !may_tune || 2.0 * double(M) * double(N) * double(K) < kTuneFlops) return def;
   std::vector<TcChoice> cand;
-  for (int p = 0; p <= (pair_ok ? 1 : 0); ++p) {
-    const int h = heuristic(p == 1);
+  for (int f = 0; f <= (pair_ok ? 2 : 0); ++f) {
+    const int h = heuristic(f != 0);
     for (int sp : {h, std::max(1, h / 2), std::min(512, 2 * h)}) {
       bool dup = false;
-      for (const auto& c : cand) dup = dup || (c.pair == (p == 1) && c.split == sp);
-      if (!dup) cand.push_back(TcChoice{p == 1, sp});
+      for (const auto& c : cand) dup = dup || (c.form == f && c.split == sp);
+      if (!dup) cand.push_back(TcChoice{f, sp});
     }
   }
   cudaEvent_t ev[2];
@@ -1467,7 +1500,7 @@ TcChoice tuned_choice(int prec, int64_t M, int64_t N, int64_t K, int n_contig, b
   float best_ms = 1e30f;
   for (const auto& c : cand) {
     TATRG_CUDA(cudaEventRecord(ev[0], s));
-    run(c.pair, c.split);
+    run(c.form, c.split);
     TATRG_CUDA(cudaEventRecord(ev[1], s));
     TATRG_CUDA(cudaEventSynchronize(ev[1]));
     float ms = 0.f;
@@ -1482,7 +1515,8 @@ TcChoice tuned_choice(int prec, int64_t M, int64_t N, int64_t K, int n_contig, b
   }();
   if (log)
     fprintf(stderr, "tatrg autotune: M=%lld N=%lld K=%lld prec=%d -> %s split %d (%.3f ms of %zu candidates)\n",
-            (long long)M, (long long)N, (long long)K, prec, best.pair ? "pair" : "single", best.split, best_ms,
+            (long long)M, (long long)N, (long long)K, prec,
+            best.form == 2 ? "multicast cluster" : best.form == 1 ? "pair" : "single", best.split, best_ms,
             cand.size());
   std::lock_guard<std::mutex> l(mu);
   cache[key] = best;
@@ -1555,7 +1589,7 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
       pack(gen_b ? nullptr : B, rn, kn, N, (Np / PK_R) * cdiv(Kp, PK_K), db, gen_b ? 0 : rcb, gen_b != nullptr);
     }
   }
-  TcMaps maps1{}, maps2{};  // B boxes of a whole tile's columns (single CTAs) or half (pairs)
+  TcMaps maps1{}, maps2{};  // B boxes of a whole tile's columns (single CTAs) or half (clusters)
   for (int p = 0; p < ns; ++p) {
     maps1.a[p] = maps2.a[p] = make_map(da.p[p], Mp, Kp, esize, TC_BM, kind);
     maps1.b[p] = make_map(db.p[p], Np, Kp, esize, BN, kind);
@@ -1578,10 +1612,10 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   }
   a.C = C;
   a.ntiles = int(Np / BN);
-  // one launch of configuration (pair, split): C is rewritten whole (zeroed first when K is
-  // split, the CTAs then add their partial sums)
-  auto run = [&](bool pair, int split) {
-    const int tile_m = pair ? 2 * TC_BM : TC_BM;
+  // one launch of configuration (tile form, split): C is rewritten whole (zeroed first when
+  // K is split, the CTAs then add their partial sums)
+  auto run = [&](int form, int split) {
+    const int tile_m = form != 0 ? 2 * TC_BM : TC_BM;
     TcArgs g = a;
     g.mtiles = int(cdiv(M, tile_m));
     const int per = int(cdiv(nkb, split));
@@ -1594,13 +1628,16 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
     }
     const int64_t units = int64_t(g.mtiles) * g.ntiles * g.split;
     TATRG_CHECK(units < (int64_t(1) << 31), TATRG_EINVAL, "gemm_tc: too many work units");
-    const TcMaps& mp = pair ? maps2 : maps1;
-    if (prec == 1 && pair) launch<1, 2, true>(mp, g, units, s);
-    else if (prec == 1) launch<1, 2, false>(mp, g, units, s);
-    else if (prec == 2 && pair) launch<2, 2, true>(mp, g, units, s);
-    else if (prec == 2) launch<2, 2, false>(mp, g, units, s);
-    else if (pair) launch<2, 3, true>(mp, g, units, s);
-    else launch<2, 3, false>(mp, g, units, s);
+    const TcMaps& mp = form != 0 ? maps2 : maps1;
+    if (prec == 1 && form == 1) launch<1, 2, 1>(mp, g, units, s);
+    else if (prec == 1 && form == 2) launch<1, 2, 2>(mp, g, units, s);
+    else if (prec == 1) launch<1, 2, 0>(mp, g, units, s);
+    else if (prec == 2 && form == 1) launch<2, 2, 1>(mp, g, units, s);
+    else if (prec == 2 && form == 2) launch<2, 2, 2>(mp, g, units, s);
+    else if (prec == 2) launch<2, 2, 0>(mp, g, units, s);
+    else if (form == 1) launch<2, 3, 1>(mp, g, units, s);
+    else if (form == 2) launch<2, 3, 2>(mp, g, units, s);
+    else launch<2, 3, 0>(mp, g, units, s);
     return g.split;
   };
   // the split-K heuristic: enough work units for two per CTA (pair)
@@ -1614,7 +1651,7 @@ void gemm_tc(const GemmDesc& d, const double* A, const double* B, double* C, int
   const TcChoice ch = tuned_choice(prec, M, N, K, a.n_contig, pair_ok, d.beta == 0.0, heuristic, run, s);
   const bool timed = st && st->timing;
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
-  const int split = run(ch.pair, ch.split);
+  const int split = run(ch.form, ch.split);
   if (timed) TATRG_CUDA(cudaEventRecord(st->next_event(), s));
   if (st) {
     st->launches += 3 + (split > 1);

@@ -72,6 +72,6 @@ def test_building_blocks_reject_bad_sizes_before_touching_memory(libpath):
     assert L.tatrg_philox_words(1, 2, 0, 0, -1, fake, None) == 1
     assert L.tatrg_philox_words(1, 2, 0, 0, 4, None, None) == 1
     assert L.tatrg_set_barrier_limit_ns(-1) == 1
-    # the CTA-pair policy: -1, 0 or 1
-    assert L.tatrg_set_cta_pairs(2) == 1
+    # the two-CTA tile policy: -1, 0, 1 or 2
+    assert L.tatrg_set_cta_pairs(3) == 1
     assert L.tatrg_set_cta_pairs(-2) == 1

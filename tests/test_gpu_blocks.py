@@ -227,10 +227,12 @@ def test_contract_tensor_core_plain(torch, prec):
     assert err < TC_TOL[prec], err
 
 
-@pytest.fixture
-def cta_pairs(torch):
-    """CTA pairs wherever they apply (M >= 1024) for the duration of a test."""
-    tg.set_cta_pairs(1)
+@pytest.fixture(params=[1, 2], ids=["cta_pair", "multicast"])
+def cta_pairs(torch, request):
+    """A two-CTA tile form wherever it applies (M >= 1024) for the duration of a test: CTA
+    pairs (one cta_group::2 MMA per 256 x 128 tile) or multicast clusters (two 128 x 128
+    tiles sharing the B tile)."""
+    tg.set_cta_pairs(request.param)
     yield
     tg.set_cta_pairs(0)
 
@@ -238,8 +240,8 @@ def cta_pairs(torch):
 @pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 @pytest.mark.parametrize("M,N,K", [(1037, 300, 517), (1024, 256, 4096), (2500, 130, 64), (4099, 1000, 33)])
 def test_contract_tensor_core_cta_pair_tiles(torch, cta_pairs, prec, M, N, K):
-    """M >= 1024 takes 256 x 128 tiles on CTA pairs: ragged last tile rows and columns, a
-    split K (few tiles, long K: float64 atomics), a single K slice."""
+    """M >= 1024 on the two-CTA tile forms (256-row work units): ragged last tile rows and
+    columns, a split K (few tiles, long K: float64 atomics), a single K slice."""
     rng = np.random.default_rng(M + N + K)
     A = rng.standard_normal((M, K))
     B = rng.standard_normal((K, N))
@@ -252,7 +254,7 @@ def test_contract_tensor_core_cta_pair_tiles(torch, cta_pairs, prec, M, N, K):
 
 @pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
 def test_contract_tensor_core_cta_pair_multimode(torch, cta_pairs, prec):
-    """Permuted multi-mode operands and output on the CTA-pair path (M = 37 * 41 >= 1024)."""
+    """Permuted multi-mode operands and output on the two-CTA tile forms (M = 37 * 41 >= 1024)."""
     rng = np.random.default_rng(14)
     I, J, a, b, K, L = 37, 29, 41, 11, 13, 17
     A = rng.standard_normal((K, I, L, a))

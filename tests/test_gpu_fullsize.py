@@ -1,6 +1,6 @@
 """The two largest contractions of the chi = 48, r = 3 step (Eqs. 6-7, C2 and C4) at their
-full shapes, through tatrg_contract with the multi-mode strides the step uses, so that the
-tensor-core path runs in the launch configuration the benchmark times.  Inputs are seeded
+full shapes, through tatrg_contract with the multi-mode strides the step uses, in each tile
+form of the tensor-core path (single CTAs, CTA pairs, multicast clusters).  Inputs are seeded
 normal operands drawn on the device; each of 2000 sampled outputs is checked against its
 float64 dot product, formed on the host from the operand entries it sums."""
 import numpy as np
@@ -30,8 +30,20 @@ def _err(got, want):
     return np.max(np.abs(got - want)) / np.max(np.abs(want))
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
-def test_c2_full_shape_sampled(torch, prec):
+# (precision, tile form): -1 single CTAs, 1 CTA pairs, 2 multicast clusters (tatrg_set_cta_pairs)
+FORMS = [(tg.TF32X3, -1), (tg.TF32X3, 1), (tg.TF32X3, 2), (tg.BF16X3, -1), (tg.BF16X3, 2),
+         (tg.BF16X6, -1), (tg.BF16X6, 2), (tg.OZAKI, 0)]
+
+
+@pytest.fixture
+def form(request):
+    tg.set_cta_pairs(request.param)
+    yield request.param
+    tg.set_cta_pairs(0)
+
+
+@pytest.mark.parametrize("prec,form", FORMS, indirect=["form"])
+def test_c2_full_shape_sampled(torch, prec, form):
     """C2: q[i0,kA,k,kX,g] = sum_{a,b} em[i0,kA,a,b,k] F[a,kX,b,g];
     M = 331776, N = 6912, K = 2304 (18 GB float64 output)."""
     em = synth.device_normal(41, (D0 * KA, Da, Ds, Ks))
@@ -54,12 +66,12 @@ def test_c2_full_shape_sampled(torch, prec):
     got = q[dev(r_ik), dev(r_k), dev(c_x), dev(c_g)].cpu().numpy()
     del em, F, q
     torch.cuda.empty_cache()
-    print("precision %d: max relative error %.3e" % (prec, _err(got, want)))
+    print("precision %d form %d: max relative error %.3e" % (prec, form, _err(got, want)))
     assert _err(got, want) < TOL[prec], _err(got, want)
 
 
-@pytest.mark.parametrize("prec", [tg.TF32X3, tg.BF16X3, tg.BF16X6, tg.OZAKI])
-def test_c4_full_shape_sampled(torch, prec):
+@pytest.mark.parametrize("prec,form", FORMS, indirect=["form"])
+def test_c4_full_shape_sampled(torch, prec, form):
     """C4: out[i0,kG,k,g] = sum_{kA,kX} q[i0,kA,k,kX,g] P[kA,kX,kG];
     M = 110592, N = 2304, K = 20736 (the 18 GB intermediate q as operand)."""
     q = synth.device_normal(44, (D0, KA, Ks, KX, Dg))
@@ -82,5 +94,5 @@ def test_c4_full_shape_sampled(torch, prec):
     got = out[dev(r_i), dev(c_u), dev(r_k), dev(r_g)].cpu().numpy()
     del q, P, out
     torch.cuda.empty_cache()
-    print("precision %d: max relative error %.3e" % (prec, _err(got, want)))
+    print("precision %d form %d: max relative error %.3e" % (prec, form, _err(got, want)))
     assert _err(got, want) < TOL[prec], _err(got, want)

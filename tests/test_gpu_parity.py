@@ -201,6 +201,7 @@ def test_split_precision_free_energy_within_1e8(prec):
     ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"], precision=prec,
                      split_from_step=start).init_ising(c["beta"], c["h"], c["d"])
     lnz = ctx.rg_step(c["steps"]).lnZ()
+    print("precision %d from step %d: rel ln Z %.3e" % (prec, start, abs(lnz - g["lnz"]) / abs(g["lnz"])))
     assert abs(lnz - g["lnz"]) < 1e-8 * abs(g["lnz"]), (lnz, g["lnz"])
 
 
@@ -225,11 +226,15 @@ def test_order_parameter_matches_oracle_and_sweep():
         assert abs(ctx.order_parameter(leg) - want) < 1e-10 * want
     betas = [0.12, 0.1497, 0.2]
     z, x = tg.Context(8, 2, 2, seed=3, sweep_workers=2).sweep_observables(betas, 0.0, 4, 10)
+    assert x.shape == (3, 10)
     for i, b in enumerate(betas):
-        r = trg.Run(b, 0.0, 4, trg.Params(8, 2, q=2, seed=3, replica=i)).step(10)
+        r = trg.Run(b, 0.0, 4, trg.Params(8, 2, q=2, seed=3, replica=i))
+        for m in range(10):  # X^(m) after every step
+            r.step()
+            want = trg.order_parameter_x(r.A, r.s, r.B, 3)[0]
+            assert abs(x[i, m] - want) < 1e-9 * want, (i, m)
         assert abs(z[i] - r.lnz()) < 1e-11 * abs(r.lnz())
-        assert abs(x[i] - trg.order_parameter_x(r.A, r.s, r.B, 3)[0]) < 1e-9 * x[i]
-    assert x[2] > 1.5 > x[0]  # ordered at beta = 0.2, disordered at 0.12 (4D: beta_c ~ 0.1497)
+    assert x[2, -1] > 1.5 > x[0, -1]  # ordered at beta = 0.2, disordered at 0.12 (4D: beta_c ~ 0.1497)
 
 
 def test_precision_schedule_from_step_5_within_1e8():
@@ -246,10 +251,12 @@ def test_precision_schedule_from_step_5_within_1e8():
 
 
 def test_ozaki_whole_run_tracks_the_oracle():
-    """chi = 24, 40 steps with the Ozaki slices from step 1: every ln c_k of the first 12
-    steps within 1e-9 relative of the oracle's and ln Z / V within 1e-9.  (Later steps drift
-    apart along the trajectory as rounding differences do in the FP64 run, see
-    test_full_run_matches_oracle; ln Z weighs them by 2^-k.)"""
+    """chi = 24, 40 steps with the Ozaki slices from step 1: ln Z / V within 1e-9 relative of
+    the oracle's, ln c_k of steps 1-4 within 1e-9 and of steps 5-12 within 5e-8.  One Ozaki
+    step perturbs ln c_k by ~1e-10 (the teacher-forced steps), and the trajectory amplifies
+    a difference about twice per step (the oracle's own rounding envelope: 2^-50 relative
+    noise on the initial split grows to 4.7e-8 by step 29), so by step 12 the runs differ
+    by up to ~1e-10 * 2^8; ln Z / V weighs step k by 2^-k."""
     g = _gold("c2_chi24")
     c = g["config"]
     ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"], precision=tg.OZAKI,
@@ -262,5 +269,5 @@ def test_ozaki_whole_run_tracks_the_oracle():
     rel = abs(lnz - g["lnz"]) / abs(g["lnz"])
     print("ozaki from step 1: rel ln Z %.3e; ln c_k errors by step: %s"
           % (rel, " ".join("%.0e" % e for e in errs)))
-    assert max(errs[:12]) < 1e-9 and rel < 1e-9
+    assert rel < 1e-9 and max(errs[:4]) < 1e-9 and max(errs[4:12]) < 5e-8
 
