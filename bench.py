@@ -405,8 +405,9 @@ def run_methods(args):
     for method, mname in ((tg.TRIAD, "triad"), (tg.ATRG, "atrg")):
         for chi in chis:
             # ATRG as the triad with identity isometries (k = chi^2) holds the squeezer
-            # environment of k^4 = chi^8 doubles: runs whose environment exceeds 100 GB are skipped
-            if method == tg.ATRG and 8.0 * chi ** 8 > 100e9:
+            # environment of k^4 = chi^8 doubles: runs whose environment exceeds 40 GB are
+            # skipped (chi = 18, 88 GB, ran out of device memory)
+            if method == tg.ATRG and 8.0 * chi ** 8 > 40e9:
                 skipped["atrg_%d" % chi] = "squeezer environment of 8 chi^8 = %.0f GB" % (8.0 * chi ** 8 / 1e9)
                 continue
             ctx = tg.Context(chi, r, Q, method=method, seed=SEED, precision=prec, stream=stream)
@@ -456,56 +457,81 @@ def run_c5(args):
     """The derivative configuration: chi = 32, r = 2, q = 2, 32 steps, beta = 0.1497,
     h in --c5-h (comma separated; default 1e-3), seed 4.  The forward-mode derivatives of
     tatrg_grad (dlnZ/dbeta, dlnZ/dh, d2lnZ/dbeta2 per site; its tangent passes run
-    concurrently) against central differences of the GPU's own FP64 ln Z / V: step 1e-5 for
-    the first derivatives, 1e-4 for the second (whose centre value is the run the derivatives
-    are taken of).  The difference runs are independent and run on concurrent threads and
-    streams.  Writes profiles/c5_grad_chi32.json after each h; prints one JSON line per h."""
+    concurrently) against central differences of the GPU's own FP64 ln Z / V for each step
+    of --c5-eps (first derivatives) and --c5-eps2 (second derivative, whose centre value is
+    the run the derivatives are taken of).  The computed ln Z / V is only piecewise smooth
+    (a truncation that changes with beta moves it by up to the truncation error), so a
+    difference is a derivative only while its stencil stays inside one smooth piece: pairs
+    of steps (e, 2e) that agree show it.  The difference runs are independent and run on
+    concurrent threads and streams.  With --c5-reuse, the tangents and differences already
+    stored for the same h are kept and only the missing steps run.  Writes
+    profiles/c5_grad_chi32.json after each h; prints one JSON line per h."""
     import concurrent.futures as cf
     import torch
     import paper_2412_14104_gb300 as tg
     torch.cuda.set_device(0)
     chi, r, steps, seed, beta = 32, 2, 32, 4, 0.1497
+    eps1 = [float(x) for x in args.c5_eps.split(",")]
+    eps2 = [float(x) for x in args.c5_eps2.split(",")]
 
     def lnz(b, h):
         st = torch.cuda.Stream()
         t0 = time.perf_counter()
         with torch.cuda.stream(st):
             z = tg.Context(chi, r, Q, seed=seed, stream=st).init_ising(b, h, 4).rg_step(steps).lnZ()
-        print("  run beta=%.6f h=%g: lnZ/V %.16f (%.0f s)" % (b, h, z, time.perf_counter() - t0), flush=True)
+        print("  run beta=%.9f h=%.9g: lnZ/V %.16f (%.0f s)" % (b, h, z, time.perf_counter() - t0), flush=True)
         return z
 
-    out = {}
+    stored = {}
+    if args.c5_reuse and os.path.exists(C5_FILE):
+        with open(C5_FILE) as f:
+            stored = json.load(f).get("results", {})
+    out = dict(stored)
     for h in [float(x) for x in args.c5_h.split(",")]:
-        t0 = time.perf_counter()
-        ctx = tg.Context(chi, r, Q, seed=seed).init_ising(beta, h, 4).rg_step(steps)
-        z0 = ctx.lnZ()
-        t_run = time.perf_counter() - t0
-        print("  run beta=%.6f h=%g: lnZ/V %.16f (%.0f s)" % (beta, h, z0, t_run), flush=True)
-        t0 = time.perf_counter()
-        gb, gh, c2 = ctx.grad(second=True)
-        t_grad = time.perf_counter() - t0
-        print("  tangents: %.12g %.12g %.12g (%.0f s)" % (gb, gh, c2, t_grad), flush=True)
-        e1, e2 = 1e-5, 1e-4
-        pts = [(beta + d, h) for d in (-e2, -e1, e1, e2)]
-        if h != 0.0:
-            pts += [(beta, h + e1), (beta, h - e1)]
+        key = "h=%g" % h
+        row = dict(stored.get(key, {}))
+        if "dlnz_dbeta" not in row:
+            t0 = time.perf_counter()
+            ctx = tg.Context(chi, r, Q, seed=seed).init_ising(beta, h, 4).rg_step(steps)
+            row["lnz"] = ctx.lnZ()
+            row["run_s"] = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            row["dlnz_dbeta"], row["dlnz_dh"], row["d2lnz_dbeta2"] = ctx.grad(second=True)
+            row["grad_s"] = time.perf_counter() - t0
+            ctx.close()
+        print("  tangents: %.12g %.12g %.12g" % (row["dlnz_dbeta"], row["dlnz_dh"], row["d2lnz_dbeta2"]), flush=True)
+        fd = row.setdefault("differences", {})
+        need = []
+        for e in eps1:
+            if "dbeta %g" % e not in fd:
+                need += [(beta + e, h), (beta - e, h)]
+            if h != 0.0 and "dh %g" % e not in fd:
+                need += [(beta, h + e), (beta, h - e)]
+        for e in eps2:
+            if "d2beta %g" % e not in fd:
+                need += [(beta + e, h), (beta - e, h)]
+        need = sorted(set(need))
         t0 = time.perf_counter()
         with cf.ThreadPoolExecutor(max_workers=3) as ex:
-            zs = dict(zip(pts, ex.map(lambda bh: lnz(*bh), pts)))
-        t_fd = time.perf_counter() - t0
-        fd_b = (zs[(beta + e1, h)] - zs[(beta - e1, h)]) / (2 * e1)
-        fd_c = (zs[(beta + e2, h)] - 2 * z0 + zs[(beta - e2, h)]) / (e2 * e2)
-        row = {"lnz": z0, "run_s": t_run,
-               "dlnz_dbeta": gb, "fd_dlnz_dbeta": fd_b, "rel_dbeta": abs(gb - fd_b) / abs(fd_b),
-               "d2lnz_dbeta2": c2, "fd_d2lnz_dbeta2": fd_c, "rel_d2beta": abs(c2 - fd_c) / abs(fd_c),
-               "grad_s": t_grad, "fd_runs_s": t_fd, "fd_runs": len(pts)}
-        if h != 0.0:
-            fd_h = (zs[(beta, h + e1)] - zs[(beta, h - e1)]) / (2 * e1)
-            row.update({"dlnz_dh": gh, "fd_dlnz_dh": fd_h, "rel_dh": abs(gh - fd_h) / abs(fd_h)})
-        out["h=%g" % h] = row
+            zs = dict(zip(need, ex.map(lambda bh: lnz(*bh), need)))
+        row["fd_runs_s"] = row.get("fd_runs_s", 0.0) + time.perf_counter() - t0
+        z0 = row["lnz"]
+        for e in eps1:
+            if "dbeta %g" % e not in fd:
+                v = (zs[(beta + e, h)] - zs[(beta - e, h)]) / (2 * e)
+                fd["dbeta %g" % e] = {"fd": v, "rel_to_tangent": abs(row["dlnz_dbeta"] - v) / abs(v)}
+            if h != 0.0 and "dh %g" % e not in fd:
+                v = (zs[(beta, h + e)] - zs[(beta, h - e)]) / (2 * e)
+                fd["dh %g" % e] = {"fd": v, "rel_to_tangent": abs(row["dlnz_dh"] - v) / abs(v)}
+        for e in eps2:
+            if "d2beta %g" % e not in fd:
+                v = (zs[(beta + e, h)] - 2 * z0 + zs[(beta - e, h)]) / (e * e)
+                fd["d2beta %g" % e] = {"fd": v, "rel_to_tangent": abs(row["d2lnz_dbeta2"] - v) / abs(v)}
+        out[key] = row
         print(json.dumps({"h": h, **row}), flush=True)
         doc = {"config": "chi=32 r=2 q=2, 32 steps, beta=0.1497, seed 4, d=4, FP64",
-               "command": "python bench.py --c5-run --c5-h " + args.c5_h,
+               "command": "python bench.py --c5-run --c5-h %s --c5-eps %s --c5-eps2 %s%s"
+                          % (args.c5_h, args.c5_eps, args.c5_eps2, " --c5-reuse" if args.c5_reuse else ""),
                "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "results": out}
         os.makedirs(os.path.dirname(C5_FILE), exist_ok=True)
         with open(C5_FILE, "w") as f:
@@ -685,11 +711,13 @@ def run_ours(args, world, rank, local):
     # the split forms issue 3 (6 for bf16x6) tensor-core products per algorithmic one
     achieved = tc_flops / (tc_ms / 1e3) / 1e12 if tc_ms > 0 else None
     nprod = {tg.BF16X6: 6.0, tg.OZAKI: 15.0}.get(prec, 3.0)
-    traffic = None  # DRAM bytes per launch from the committed ncu capture of this workload
-    prof = os.path.join(ROOT, "profiles", "tc_gemm_chi48_traffic.json")
-    if os.path.exists(prof) and (chi, r) == (CHI, R) and prec == tg.TF32X3:
+    # DRAM traffic: no capture of this workload's launches (tens of GB resident); the
+    # committed one-launch capture of the chi = 32 C2 contraction stands beside it
+    traffic_sample = None
+    prof = os.path.join(ROOT, "profiles", "tc_gemm_c2_chi32_traffic.json")
+    if os.path.exists(prof):
         with open(prof) as f:
-            traffic = json.load(f).get("dram_bytes_per_launch")
+            traffic_sample = json.load(f)
 
     fp64_ms = None
     if args.fp64_steps > 0 and prec != tg.FP64:
@@ -725,7 +753,10 @@ def run_ours(args, world, rank, local):
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None,
                      "frac_algorithmic": (achieved / peak) if achieved else None,
-                     "traffic": traffic, "peak_source": note,
+                     "traffic": None,
+                     "traffic_note": "not captured on this workload; traffic_sample is one ncu "
+                                     "capture of the chi = 32 C2 launch (same kernel, 3xTF32)",
+                     "traffic_sample": traffic_sample, "peak_source": note,
                      "launches": tc_launches, "launches_note": "tensor-core launches on the "
                      "context's stream; the small GEMMs of the factorisations that run concurrently "
                      "on worker streams are not timed here",
@@ -793,6 +824,9 @@ def main():
     ap.add_argument("--c5-run", action="store_true",
                     help="derivatives at chi = 32, 32 steps against central differences")
     ap.add_argument("--c5-h", default="1e-3")
+    ap.add_argument("--c5-eps", default="1e-5,1e-7,2e-7", help="difference steps of the first derivatives")
+    ap.add_argument("--c5-eps2", default="1e-4,1e-6,2e-6", help="difference steps of the second derivative")
+    ap.add_argument("--c5-reuse", action="store_true", help="keep stored tangents and differences")
     ap.add_argument("--c4-run", action="store_true", help="the 64-temperature sweep at chi = 32")
     ap.add_argument("--sweep-workers", type=int, default=8)
     ap.add_argument("--c4-serial", type=int, default=16,

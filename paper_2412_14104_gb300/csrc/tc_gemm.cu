@@ -122,6 +122,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+// hint: bring a box into L2 ahead of its load (no shared memory, no barrier)
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
+}
 // the same box written to the same shared-memory offset of every CTA in `mask` (a cluster of
 // this GPU's own CTAs), each of whose barriers at `bar`'s offset receives the bytes it got
 __device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
@@ -330,6 +337,11 @@ __device__ __forceinline__ void two_sum_acc2(uint64_t& hi, uint64_t& lo, uint64_
   hi = s;
 }
 
+// K stages ahead of the producer whose operand boxes are prefetched into L2 (0: none)
+#ifndef TATRG_L2_PREFETCH
+#define TATRG_L2_PREFETCH 0
+#endif
+
 // Output tile of work unit u: grouped raster (GROUP_M consecutive row panels sweep all
 // column panels together, so the CTAs working at one time share a few A and B panels
 // that stay in L2) and the K range of its split index.
@@ -468,13 +480,23 @@ __global__ void __maxnreg__(96)  // 18 warps x 96 registers fit one SM's registe
       bool ok = true;
       for (int u = first; u < units && ok; u += stride) {
         const Unit w = unit_of<TILE_M>(g, u);
+        const int ya = int(w.m0) + int(rank) * TC_BM, yb = int(w.n0) + int(rank) * B_LOAD;
+        auto prefetch = [&](int j) {
+#pragma unroll
+          for (int p = 0; p < NS; ++p) {
+            tma_prefetch_2d(&maps.a[p], (w.kb0 + j) * KELEM, ya);
+            tma_prefetch_2d(&maps.b[p], (w.kb0 + j) * KELEM, yb);
+          }
+        };
+        if (TATRG_L2_PREFETCH > 0)
+          for (int j = 0; j < min(TATRG_L2_PREFETCH, w.nk); ++j) prefetch(j);
         for (int i = 0; i < w.nk; ++i, ++it) {
+          if (TATRG_L2_PREFETCH > 0 && i + TATRG_L2_PREFETCH < w.nk) prefetch(i + TATRG_L2_PREFETCH);
           const int s = it % STAGES, round = it / STAGES;
           if (round > 0 && !mbar_wait<CLU>(&empty_bar[s], (round - 1) & 1, now_ns() + WAIT_NS)) { ok = false; break; }
           uint8_t* st = smem + s * STAGE;
           mbar_expect_tx(&full_bar[s], STAGE);  // FORM 2: half of B comes from the other CTA
           const int kx = (w.kb0 + i) * KELEM;
-          const int ya = int(w.m0) + int(rank) * TC_BM, yb = int(w.n0) + int(rank) * B_LOAD;
 #pragma unroll
           for (int p = 0; p < NS; ++p) {
             tma_load_2d(st + p * A_TILE, &maps.a[p], &full_bar[s], kx, ya);
