@@ -471,8 +471,8 @@ def run_c5(args):
     import paper_2412_14104_gb300 as tg
     torch.cuda.set_device(0)
     chi, r, steps, seed, beta = 32, 2, 32, 4, 0.1497
-    eps1 = [float(x) for x in args.c5_eps.split(",")]
-    eps2 = [float(x) for x in args.c5_eps2.split(",")]
+    eps1 = [float(x) for x in args.c5_eps.split(",") if x]
+    eps2 = [float(x) for x in args.c5_eps2.split(",") if x]
 
     def lnz(b, h):
         st = torch.cuda.Stream()
