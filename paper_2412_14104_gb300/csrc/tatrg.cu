@@ -967,7 +967,55 @@ void tatrg_ctx::rg_step() {
              modes({{Da_, Ds * Da_ * Ds, Ds * Da_}, {Da_, Ds, 1}})),
            gam.d(), tp(gamd), eta.d(), tp(etad), rhoR[d - 2].d(), tp(rhoRd[d - 2]));
     }
-    if (g > 0) {
+    if (g > 0 && p.method == TATRG_ATRG) {
+      // ATRG: the group isometries I..L are identities, so the pair Gram of group leg nu is
+      // the environment traced over the other group leg z.  With
+      //   Q_E[x,a,y,b] = sum_{i0,z,s} E[i0,(x,z),s,a] E[i0,(y,z),s,b],
+      //   Q_F[a,x,b,y] = sum_{z,s,g} Fy[a,(x,z),s,g] F[b,(y,z),s,g],
+      // rho_L[(x,x'),(y,y')] = sum_{a,b} Q_E[x,a,y,b] Q_F[a,x',b,y'], and rho_R likewise from
+      // Gx, G and H: chi^4 intermediates and O(chi^7) work in place of the chi^8 environment
+      // that the general triad contraction below would build for k = chi^2 (the same sums).
+      for (int nu = 1; nu <= g; ++nu) {
+        const int64_t Dn = D[nu], Dz = Gd / Dn;
+        const int64_t snu = prod(D, nu + 1, 1 + g);  // stride of leg nu in the group index
+        const int64_t sz = nu == 1 ? 1 : Dn;          // stride of the other group leg (g == 2)
+        const int64_t Pn = Dn * Dn, QQ = Dn * Da_ * Dn * Da_;
+        DevBuf qe(QQ * sizeof(double), st), qf(QQ * sizeof(double), st);
+        DevBuf qed = tbuf(QQ), qfd = tbuf(QQ);
+        run2(ST_SQUEEZE,
+             G(modes({{Dn, snu * Ds * Da_, Da_ * Dn * Da_}, {Da_, 1, Dn * Da_}}),
+               modes({{Dn, snu * Ds * Da_, Da_}, {Da_, 1, 1}}),
+               modes({{D0, KA * Ds * Da_, KA * Ds * Da_}, {Dz, sz * Ds * Da_, sz * Ds * Da_}, {Ds, Da_, Da_}})),
+             E.d(), tp(Ed), E.d(), tp(Ed), qe.d(), tp(qed));
+        run2(ST_SQUEEZE,
+             G(modes({{Da_, KX * Ds * Dg, Dn * Da_ * Dn}, {Dn, snu * Ds * Dg, Da_ * Dn}}),
+               modes({{Da_, KX * Ds * Dg, Dn}, {Dn, snu * Ds * Dg, 1}}),
+               modes({{Dz, sz * Ds * Dg, sz * Ds * Dg}, {Ds * Dg, 1, 1}})),
+             Fy.d(), tp(Fyd), F.d(), tp(Fd), qf.d(), tp(qfd));
+        // rho[x,x',y,y'] = sum_{a,b} Q1[x,a,y,b] Q2[a,x',b,y'] (row-major (x,x') x (y,y'))
+        const GemmDesc pair = G(modes({{Dn, Da_ * Dn * Da_, Dn * Dn * Dn}, {Dn, Da_, Dn}}),
+                                modes({{Dn, Da_ * Dn, Dn * Dn}, {Dn, 1, 1}}),
+                                modes({{Da_, Dn * Da_, Dn * Da_ * Dn}, {Da_, 1, Dn}}));
+        rhoL[nu - 1] = DevBuf(Pn * Pn * sizeof(double), st);
+        rhoLd[nu - 1] = tbuf(Pn * Pn);
+        run2(ST_SQUEEZE, pair, qe.d(), tp(qed), qf.d(), tp(qfd), rhoL[nu - 1].d(), tp(rhoLd[nu - 1]));
+        // Q_G[x,b,y,c] = sum_{z,s,g} Gx[b,(x,z),s,g] G[c,(y,z),s,g]
+        run2(ST_SQUEEZE,
+             G(modes({{Dn, snu * Ds * Dg, Da_ * Dn * Da_}, {Da_, KY * Ds * Dg, Dn * Da_}}),
+               modes({{Dn, snu * Ds * Dg, Da_}, {Da_, KY * Ds * Dg, 1}}),
+               modes({{Dz, sz * Ds * Dg, sz * Ds * Dg}, {Ds * Dg, 1, 1}})),
+             Gx.d(), tp(Gxd), Gt.d(), tp(Gtd), qe.d(), tp(qed));
+        // Q_H[b,x,c,y] = sum_{j0,z,s} H[j0,(x,z),s,b] H[j0,(y,z),s,c]
+        run2(ST_SQUEEZE,
+             G(modes({{Da_, 1, Dn * Da_ * Dn}, {Dn, snu * Ds * Da_, Da_ * Dn}}),
+               modes({{Da_, 1, Dn}, {Dn, snu * Ds * Da_, 1}}),
+               modes({{D0, KD * Ds * Da_, KD * Ds * Da_}, {Dz, sz * Ds * Da_, sz * Ds * Da_}, {Ds, Da_, Da_}})),
+             H.d(), tp(Hd), H.d(), tp(Hd), qf.d(), tp(qfd));
+        rhoR[nu - 1] = DevBuf(Pn * Pn * sizeof(double), st);
+        rhoRd[nu - 1] = tbuf(Pn * Pn);
+        run2(ST_SQUEEZE, pair, qe.d(), tp(qed), qf.d(), tp(qfd), rhoR[nu - 1].d(), tp(rhoRd[nu - 1]));
+      }
+    } else if (g > 0) {
       // Env_L[kA,kA',kX,kX'] = sum_{a,a'} P_E[kA,kA',a,a'] P_F[a,a',kX,kX']
       DevBuf pe(KA * KA * Da_ * Da_ * sizeof(double), st), pf(Da_ * Da_ * KX * KX * sizeof(double), st);
       DevBuf ped = tbuf(KA * KA * Da_ * Da_), pfd = tbuf(Da_ * Da_ * KX * KX);

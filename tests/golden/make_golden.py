@@ -30,17 +30,22 @@ CONFIGS = {
     # chi = 24 with the multiplet gap of the library's split-precision steps (1e-6) from
     # step 1: separates the rounding of the split forms from their cut rule
     "c2_chi24_tau6": (0.1497, 0.0, 4, 24, 2, 2, 1, 40),
+    # plain ATRG (identity isometries, the chi^9 contraction) in 4D and 3D
+    "atrg_d4_chi8": (0.1497, 1e-4, 4, 8, 2, 2, 7, 12),
+    "atrg_d3_chi8": (0.22, 0.01, 3, 8, 2, 2, 6, 12),
 }
 EXTRA = {"c2_chi24_tau6": {"split_tau": 1e-6, "split_from_step": 1}}
+METHOD = {"atrg_d4_chi8": "atrg", "atrg_d3_chi8": "atrg"}
 
 
 def run(name):
     beta, h, d, chi, r, q, seed, steps = CONFIGS[name]
     t0 = time.time()
-    p = trg.Params(chi, r, q=q, seed=seed, **EXTRA.get(name, {}))
+    method = METHOD.get(name, "triad")
+    p = trg.Params(chi, r, q=q, seed=seed, method=method, **EXTRA.get(name, {}))
     R = trg.Run(beta, h, d, p)
     out = {"config": {"beta": beta, "h": h, "d": d, "chi": chi, "r": r, "q": q, "seed": seed,
-                      "steps": steps, **EXTRA.get(name, {})},
+                      "steps": steps, "method": method, **EXTRA.get(name, {})},
            "lnc": [R.lnc[0]], "s": [R.s.tolist()], "sigma": [], "sq": [], "swap_gap": [],
            "sq_gap": [], "dims": [list(R.A.shape)], "lnz_after": []}
     for k in range(steps):

@@ -49,7 +49,8 @@ def _min_gap(g, k):
     return min([x for x in gaps if x is not None] + [math.inf])
 
 
-@pytest.mark.parametrize("name", ["c1_chi6", "d4_chi10_h", "d2_chi16", "d3_chi8", "c2_chi24"])
+@pytest.mark.parametrize("name", ["c1_chi6", "d4_chi10_h", "d2_chi16", "d3_chi8", "atrg_d4_chi8",
+                                  "atrg_d3_chi8", "c2_chi24"])
 def test_full_run_matches_oracle(name):
     """Every step's ln c_k and s', and the final ln Z / V.  A cut through a degenerate
     multiplet (relative gap < 1e-8, several correct answers) would make later values depend
@@ -67,7 +68,8 @@ def test_full_run_matches_oracle(name):
     if os.path.exists(env_path):
         with open(env_path) as f:
             env = json.load(f)
-    ctx = tg.Context(c["chi"], c["r"], c["q"], seed=c["seed"]).init_ising(c["beta"], c["h"], c["d"])
+    method = tg.ATRG if c.get("method") == "atrg" else tg.TRIAD
+    ctx = tg.Context(c["chi"], c["r"], c["q"], method=method, seed=c["seed"]).init_ising(c["beta"], c["h"], c["d"])
     tol = 1e-11
     for k in range(c["steps"]):
         ctx.rg_step()
