@@ -405,6 +405,39 @@ def test_derivative_onsager_2d():
     assert abs(got - exact) < 1e-6, (got, exact)
 
 
+def test_truncated_lnz_jumps_between_nearby_couplings():
+    """The truncated method's ln Z / V is only piecewise smooth in beta: chi = 8, r = 2, 16
+    steps, h = 1e-3 at beta = 0.1497.  Between beta - 5e-7 and beta - 2e-7 it drops by ~4e-6
+    across an interval that bisection narrows below 1e-11 (a slope above 1e5 against a
+    derivative of ~1): a step of the run picks another kept subspace there (its position
+    is a rounding-level detail of the run, its existence is not).  Central
+    differences whose stencil stays inside one piece agree (steps 1e-7 and 2e-7, to 1e-4),
+    those whose stencil spans the jump do not (step 1e-6 is off by more than a factor 2),
+    so a difference step must be chosen per point, not fixed."""
+    beta, h = 0.1497, 1e-3
+
+    def lnz(b):
+        return trg.Run(b, h, 4, trg.Params(8, 2, q=2, seed=4)).step(16).lnz()
+
+    def central(e):
+        return (lnz(beta + e) - lnz(beta - e)) / (2 * e)
+
+    d1, d2, d6 = central(1e-7), central(2e-7), central(1e-6)
+    assert abs(d1 - d2) < 1e-4 * abs(d1), (d1, d2)
+    assert abs(d6 - d1) > abs(d1), (d6, d1)
+    lo, hi = beta - 5e-7, beta - 2e-7
+    zlo, zhi = lnz(lo), lnz(hi)
+    assert zhi - zlo > 1e-6
+    while hi - lo > 1e-11:
+        mid = 0.5 * (lo + hi)
+        zm = lnz(mid)
+        if abs(zm - zlo) > abs(zhi - zm):
+            hi, zhi = mid, zm
+        else:
+            lo, zlo = mid, zm
+    assert abs(zhi - zlo) > 1e-6, (lo, hi, zhi - zlo)
+
+
 @pytest.mark.parametrize("seed", [0, 1])
 def test_squeezers_are_optimal_oblique_projectors(seed):
     """Eq. 5: the squeezer pair (M, N) built from the Grams rho_L = R_L^T R_L and
