@@ -106,6 +106,51 @@ def _dptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _reach(modes, which):
+    """Elements a mode list can address from its base pointer: 1 + the largest offset
+    sum (ext - 1) * stride over the modes, with the stride taken from position `which`
+    of each (ext, stride, stride) triple; 0 when an extent is 0."""
+    top = 0
+    for m in modes:
+        e, st = int(m[0]), int(m[which])
+        if e < 0 or st < 0:
+            raise TatrgError(1, "mode extents and strides must be non-negative, got %r" % (tuple(m),))
+        if e == 0:
+            return 0
+        top += (e - 1) * st
+    return top + 1
+
+
+def _device_ptrs(*specs):
+    """Device pointers of the caller's tensors, each spec (tensor, elements, name[, dtypes]),
+    after checking that every tensor can hold what the call will address: dtype float64
+    (unless the spec names others), contiguous, at least that many elements, then a CUDA
+    tensor on the current device.  The library reaches caller memory only through these
+    pointers and the call's sizes, so a mismatch is reported here (EINVAL) instead of
+    becoming an out-of-range access on the GPU."""
+    import torch
+    for spec in specs:
+        t, nelem, what = spec[:3]
+        dtypes = spec[3] if len(spec) > 3 else (torch.float64,)
+        if not isinstance(t, torch.Tensor):
+            raise TatrgError(1, "%s must be a torch tensor" % what)
+        if t.dtype not in dtypes:
+            raise TatrgError(1, "%s must have dtype %s, got %s" % (what, "/".join(map(str, dtypes)), t.dtype))
+        if not t.is_contiguous():
+            raise TatrgError(1, "%s must be contiguous" % what)
+        if t.numel() < nelem:
+            raise TatrgError(1, "%s holds %d elements, the call addresses %d" % (what, t.numel(), nelem))
+    out = []
+    for t, _, what, *_ in specs:
+        if not t.is_cuda:
+            raise TatrgError(1, "%s must be a CUDA tensor" % what)
+        if t.device.index != torch.cuda.current_device():
+            raise TatrgError(1, "%s is on cuda:%d, the current device is cuda:%d"
+                             % (what, t.device.index, torch.cuda.current_device()))
+        out.append(ctypes.c_void_p(t.data_ptr()))
+    return out
+
+
 def _stream_ptr(stream):
     if stream is None:
         import torch
@@ -197,7 +242,11 @@ class Context:
         return A, s, B
 
     def set_state(self, A, s, B, step, partial_lnz):
+        A, s, B = np.asarray(A), np.asarray(s), np.asarray(B)
         d = A.ndim - 1
+        if not 2 <= d <= 4 or s.ndim != 1 or A.shape[d] != s.size or B.shape != (s.size,) + A.shape[:d]:
+            raise TatrgError(1, "set_state: need A (D_0..D_{d-1}, Da), s (Da,), B (Da, D_0..D_{d-1}) "
+                                "with 2 <= d <= 4; got %s, %s, %s" % (A.shape, s.shape, B.shape))
         dims = (ctypes.c_int * 5)(*(list(A.shape[:d]) + [s.size] + [0] * (4 - d)))
         A = np.ascontiguousarray(A, dtype=np.float64)
         B = np.ascontiguousarray(B, dtype=np.float64)
@@ -215,9 +264,8 @@ class Context:
 # --- building blocks on torch CUDA tensors --------------------------------------------
 
 def gaussian(seed, stream_id, rows, cols, out, replica=0, stream=None):
-    assert out.is_cuda and out.numel() >= rows * cols
-    _check(lib().tatrg_gaussian(seed, stream_id, replica, rows, cols,
-                                ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    (po,) = _device_ptrs((out, max(rows, 0) * max(cols, 0), "out"))
+    _check(lib().tatrg_gaussian(seed, stream_id, replica, rows, cols, po, _stream_ptr(stream)))
     return out
 
 
@@ -235,13 +283,30 @@ def _contraction(m, n, k, alpha, beta):
     return c
 
 
+def _operand_ptrs(m, n, k, A, B, C):
+    """Checked pointers of a contraction's operands (B may be None: a generated sketch).
+    A is addressed through the m and k strides in A, B through n and k strides in B, C
+    through the m and n strides in C; nothing is read or written when M or N is 0."""
+    if _reach(m, 1) == 0 or _reach(n, 1) == 0:
+        need_a = need_b = need_c = 0
+    else:
+        kk = _reach(k, 1) > 0
+        need_a = _reach(m, 1) + _reach(k, 1) - 1 if kk else 0
+        need_b = _reach(n, 1) + _reach(k, 2) - 1 if kk else 0
+        need_c = _reach(m, 2) + _reach(n, 2) - 1
+    if B is None:
+        pa, pc = _device_ptrs((A, need_a, "A"), (C, need_c, "C"))
+        return pa, None, pc
+    return _device_ptrs((A, need_a, "A"), (B, need_b, "B"), (C, need_c, "C"))
+
+
 def contract_sketch(m, n, k, A, seed, stream_id, C, replica=0, alpha=1.0, beta=0.0,
                     precision=TF32X3, stream=None):
     """contract() with B the Gaussian sketch (seed, stream_id, replica) generated in the
     tensor-core operand packer instead of read from memory (split precisions only)."""
     c = _contraction(m, n, k, alpha, beta)
-    _check(lib().tatrg_contract_sketch(ctypes.byref(c), precision, ctypes.c_void_p(A.data_ptr()),
-                                       seed, stream_id, replica, ctypes.c_void_p(C.data_ptr()),
+    pa, _, pc = _operand_ptrs(m, n, k, A, None, C)
+    _check(lib().tatrg_contract_sketch(ctypes.byref(c), precision, pa, seed, stream_id, replica, pc,
                                        _stream_ptr(stream)))
     return C
 
@@ -250,42 +315,41 @@ def contract(m, n, k, A, B, C, alpha=1.0, beta=0.0, precision=FP64, stream=None)
     """C[m, n] = alpha sum_k A[m, k] B[k, n] + beta C; m = [(ext, strideA, strideC), ...],
     n = [(ext, strideB, strideC), ...], k = [(ext, strideA, strideB), ...] (outermost first)."""
     c = _contraction(m, n, k, alpha, beta)
-    _check(lib().tatrg_contract(ctypes.byref(c), precision, ctypes.c_void_p(A.data_ptr()),
-                                ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(C.data_ptr()),
-                                _stream_ptr(stream)))
+    pa, pb, pc = _operand_ptrs(m, n, k, A, B, C)
+    _check(lib().tatrg_contract(ctypes.byref(c), precision, pa, pb, pc, _stream_ptr(stream)))
     return C
 
 
 def orth(Y, Q, R, precision=FP64, stream=None):
     m, n = Y.shape
     k = ctypes.c_int()
-    _check(lib().tatrg_orth(precision, m, n, ctypes.c_void_p(Y.data_ptr()), ctypes.c_void_p(Q.data_ptr()),
-                            ctypes.c_void_p(R.data_ptr()), ctypes.byref(k), _stream_ptr(stream)))
+    py, pq, pr = _device_ptrs((Y, m * n, "Y"), (Q, m * n, "Q"), (R, n * n, "R"))
+    _check(lib().tatrg_orth(precision, m, n, py, pq, pr, ctypes.byref(k), _stream_ptr(stream)))
     return k.value
 
 
-def svd(A, U, S, V, stream=None):
+def _svd_ptrs(A, U, S, V):
     m, n = A.shape
-    _check(lib().tatrg_svd(m, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(U.data_ptr()),
-                           ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
-                           _stream_ptr(stream)))
+    return (m, n, *_device_ptrs((A, m * n, "A"), (U, m * n, "U"), (S, n, "S"), (V, n * n, "V")))
+
+
+def svd(A, U, S, V, stream=None):
+    _check(lib().tatrg_svd(*_svd_ptrs(A, U, S, V), _stream_ptr(stream)))
 
 
 def svd_noalloc(A, U, S, V, stream=None):
     """tatrg_svd_noalloc: the same SVD with its workspace in the library's fixed device
     array instead of allocated memory (for callers that cannot allocate)."""
-    m, n = A.shape
-    _check(lib().tatrg_svd_noalloc(m, n, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(U.data_ptr()),
-                                   ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
-                                   _stream_ptr(stream)))
+    _check(lib().tatrg_svd_noalloc(*_svd_ptrs(A, U, S, V), _stream_ptr(stream)))
 
 
 def philox_words(seed, stream_id, first, npairs, out, replica=0, stream=None):
     """Raw Philox4x32-10 words of counter blocks first .. first + npairs - 1 into the int32
     CUDA tensor `out` (4 words per block)."""
-    assert out.is_cuda and out.numel() >= 4 * npairs
-    _check(lib().tatrg_philox_words(seed, stream_id, replica, first, npairs,
-                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    import torch
+    words = tuple(t for t in (torch.int32, getattr(torch, "uint32", None)) if t is not None)
+    (po,) = _device_ptrs((out, 4 * max(npairs, 0), "out", words))
+    _check(lib().tatrg_philox_words(seed, stream_id, replica, first, npairs, po, _stream_ptr(stream)))
     return out
 
 

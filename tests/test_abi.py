@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -75,3 +77,60 @@ def test_building_blocks_reject_bad_sizes_before_touching_memory(libpath):
     # the two-CTA tile policy: -1, 0, 1 or 2
     assert L.tatrg_set_cta_pairs(3) == 1
     assert L.tatrg_set_cta_pairs(-2) == 1
+
+
+def test_binding_checks_caller_tensors_before_any_call():
+    """The building blocks address caller-owned device memory only through a pointer and
+    the call's sizes, which the library cannot check against an allocation it does not
+    own; the binding rejects a wrong dtype, a non-contiguous layout, too few elements for
+    the extents the call addresses, negative strides and host tensors (EINVAL), before the
+    library is called."""
+    import torch
+    import paper_2412_14104_gb300 as tg
+
+    def code(f, *a, **kw):
+        with pytest.raises(tg.TatrgError) as e:
+            f(*a, **kw)
+        return e.value.code, str(e.value)
+
+    f64 = lambda *s: torch.zeros(s, dtype=torch.float64)
+    # C[m, n] = A[m, k] B[k, n] with M, N, K = 5, 4, 3: A needs 15, B 12, C 20 elements
+    m, n, k = [(5, 3, 4)], [(4, 1, 1)], [(3, 1, 4)]
+    assert tg._reach(m, 1) == 13 and tg._reach(k, 2) == 9 and tg._reach([(0, 7, 7)], 1) == 0
+    c, msg = code(tg.contract, m, n, k, f64(15).float(), f64(12), f64(20))
+    assert c == 1 and "dtype" in msg
+    c, msg = code(tg.contract, m, n, k, f64(14), f64(12), f64(20))
+    assert c == 1 and "A holds 14 elements, the call addresses 15" in msg
+    c, msg = code(tg.contract, m, n, k, f64(15), f64(11), f64(20))
+    assert c == 1 and "B holds 11" in msg
+    c, msg = code(tg.contract, m, n, k, f64(15), f64(12), f64(19))
+    assert c == 1 and "C holds 19" in msg
+    c, msg = code(tg.contract, m, n, k, f64(15), f64(12), f64(4, 10)[:, :5])
+    assert c == 1 and "contiguous" in msg
+    c, msg = code(tg.contract, [(5, -3, 4)], n, k, f64(15), f64(12), f64(20))
+    assert c == 1 and "non-negative" in msg
+    c, msg = code(tg.contract, m, n, k, f64(15), f64(12), f64(20))
+    assert c == 1 and "CUDA tensor" in msg
+    # an empty M addresses nothing, so empty operands pass the size checks
+    c, msg = code(tg.contract, [(0, 3, 4)], n, k, f64(0), f64(12), f64(0))
+    assert "CUDA tensor" in msg
+    c, msg = code(tg.svd, f64(6, 4), f64(23), f64(4), f64(16))
+    assert c == 1 and "U holds 23" in msg
+    c, msg = code(tg.svd_noalloc, f64(6, 4), f64(24), f64(3), f64(16))
+    assert c == 1 and "S holds 3" in msg
+    c, msg = code(tg.orth, f64(6, 4), f64(24), f64(15))
+    assert c == 1 and "R holds 15" in msg
+    c, msg = code(tg.gaussian, 1, 2, 3, 4, f64(11))
+    assert c == 1 and "out holds 11" in msg
+    c, msg = code(tg.philox_words, 1, 2, 0, 3, f64(12))
+    assert c == 1 and "dtype" in msg
+    c, msg = code(tg.philox_words, 1, 2, 0, 3, torch.zeros(11, dtype=torch.int32))
+    assert c == 1 and "out holds 11" in msg
+    # host-side state: shapes must describe one split site tensor
+    ctx = object.__new__(tg.Context)
+    ctx._h = None
+    A = np.zeros((2, 2, 2, 2, 3))
+    c, msg = code(tg.Context.set_state, ctx, A, np.zeros(3), np.zeros((3, 2, 2, 2, 3)), 0, 0.0)
+    assert c == 1 and "set_state" in msg
+    c, msg = code(tg.Context.set_state, ctx, A, np.zeros(2), np.zeros((2, 2, 2, 2, 2)), 0, 0.0)
+    assert c == 1
