@@ -175,6 +175,52 @@ def test_triad_with_full_width_equals_atrg():
         assert abs(a - b) < 1e-12, (d, a, b)
 
 
+@pytest.mark.parametrize("dims", [(3, 2, 4, 2), (2, 3, 2, 3), (3, 4, 2)])
+def test_atrg_pair_grams_are_partial_traces(dims):
+    """Eq. 5 with identity isometries (ATRG): the pair Gram of a group leg equals the
+    triad-cell environment traced over the other group leg, so it can be formed from
+    Q_E[x,a,y,b] = sum E[i,(x,z),s,a] E[i,(y,z),s,b] and the like (chi^4 intermediates)
+    instead of the chi^8 environment.  Random E, F, G, H; d = 4 (two group legs) and d = 3."""
+    rng = np.random.default_rng(sum(dims))
+    d = len(dims)
+    g = d - 2
+    D0, Ds = dims[0], dims[-1]
+    gshape = tuple(dims[1:1 + g])
+    Gd = int(np.prod(gshape))
+    Da, Dg = 4, 3
+    E = rng.standard_normal((D0, Gd, Ds, Da))
+    F = rng.standard_normal((Da, Gd, Ds, Dg))
+    G = rng.standard_normal((Da, Gd, Ds, Dg))
+    H = rng.standard_normal((D0, Gd, Ds, Da))
+    I = np.eye(Gd).reshape(gshape + (Gd,))
+    rho_l, rho_r = trg.squeezer_grams(E, F, G, H, I, I, I, I, g)
+    # the environments of Eq. 5 that the general construction dresses F and G with
+    om_d = np.einsum("jksb,jksc->bc", H, H)
+    om_y = np.einsum("cksg,cksh->gh", np.einsum("bksg,bc->cksg", G, om_d), G)
+    om_a = np.einsum("iksa,iksb->ab", E, E)
+    om_x = np.einsum("bksg,bksh->gh", np.einsum("aksg,ab->bksg", F, om_a), F)
+    Fy = np.einsum("akxg,gh->akxh", F, om_y).reshape((Da,) + gshape + (Ds, Dg))
+    Gx = np.einsum("bkxg,gh->bkxh", G, om_x).reshape((Da,) + gshape + (Ds, Dg))
+    E5, F5 = E.reshape((D0,) + gshape + (Ds, Da)), F.reshape((Da,) + gshape + (Ds, Dg))
+    G5, H5 = G.reshape((Da,) + gshape + (Ds, Dg)), H.reshape((D0,) + gshape + (Ds, Da))
+    for nu in range(1, g + 1):
+        if g == 1:
+            e, f = "ixsa,iysb->xayb", "axsh,bysh->axby"
+            gg, hh = "bxsh,cysh->xbyc", "jxsb,jysc->bxcy"
+        elif nu == 1:
+            e, f = "ixzsa,iyzsb->xayb", "axzsh,byzsh->axby"
+            gg, hh = "bxzsh,cyzsh->xbyc", "jxzsb,jyzsc->bxcy"
+        else:
+            e, f = "izxsa,izysb->xayb", "azxsh,bzysh->axby"
+            gg, hh = "bzxsh,czysh->xbyc", "jzxsb,jzysc->bxcy"
+        Dn = dims[nu]
+        want_l = np.einsum("xayb,azbw->xzyw", np.einsum(e, E5, E5), np.einsum(f, Fy, F5))
+        want_r = np.einsum("xbyc,bzcw->xzyw", np.einsum(gg, Gx, G5), np.einsum(hh, H5, H5))
+        scale_l, scale_r = np.abs(want_l).max(), np.abs(want_r).max()
+        assert np.allclose(rho_l[nu - 1], want_l.reshape(Dn * Dn, Dn * Dn), atol=1e-13 * scale_l)
+        assert np.allclose(rho_r[nu - 1], want_r.reshape(Dn * Dn, Dn * Dn), atol=1e-13 * scale_r)
+
+
 def test_truncation_error_shrinks_with_chi_4d():
     """P5 (truncated): on the 2^4 torus the error of chi = 4, 6, 8 runs shrinks."""
     beta, h = 0.1497, 0.0
