@@ -67,7 +67,9 @@ typedef struct {
   int method;     /* tatrg_method */
   int precision;  /* tatrg_precision */
   unsigned long long seed; /* Philox key of all Gaussian sketches */
-  int checkpoint_every;    /* steps between checkpoints of the reverse sweep (0: 4) */
+  int checkpoint_every;    /* unused (keep 0 or any value): the derivatives of tatrg_grad
+                              are forward-mode tangents, which store nothing across steps,
+                              so there is no reverse sweep to checkpoint */
   int split_from_step;     /* steps before this one run in FP64 whatever the precision */
   int split_stages;        /* bit mask of the stages whose large contractions use the split
                               precision: 1 swap, 2 triad, 4 squeezers, 8 contraction,

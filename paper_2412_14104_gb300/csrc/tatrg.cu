@@ -1613,12 +1613,14 @@ tatrg_status tatrg_sweep_observables(tatrg_ctx* ctx, const double* betas, int nb
     tc_available();  // one-time initialisation before the workers start
     TATRG_CUDA(cudaStreamSynchronize(ctx->stream));
     std::atomic<int> next(0);
+    std::atomic<bool> failed(false);  // read by every worker between temperatures
     std::mutex mu;
     tatrg_status first = TATRG_OK;
     std::string first_msg;
     auto fail = [&](tatrg_status c, const std::string& m) {
       std::lock_guard<std::mutex> l(mu);
       if (first == TATRG_OK) { first = c; first_msg = m; }
+      failed.store(true);
     };
     std::vector<std::thread> pool;
     for (int w = 0; w < nw; ++w) {
@@ -1627,7 +1629,7 @@ tatrg_status tatrg_sweep_observables(tatrg_ctx* ctx, const double* betas, int nb
         try {
           TATRG_CUDA(cudaSetDevice(dev));
           TATRG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-          for (int i = next++; i < nbeta && first == TATRG_OK; i = next++) {
+          for (int i = next++; i < nbeta && !failed.load(); i = next++) {
             tatrg_ctx sub(ctx->p, s);
             sub.replica = uint32_t(i);
             sub.init_ising(betas[i], h, d);
@@ -1671,7 +1673,7 @@ tatrg_status tatrg_spectrum(const tatrg_ctx* ctx, int kind, double* out, int* n)
   if (kind == 0) v = &ctx->spec_s;
   else if (kind == 1) v = &ctx->spec_sigma;
   else if (kind >= 2 && size_t(kind - 2) < ctx->spec_sq.size()) v = &ctx->spec_sq[kind - 2];
-  if (!v) return TATRG_EINVAL;
+  if (!v || (out && *n < 0)) return TATRG_EINVAL;
   int cap = *n;
   *n = int(v->size());
   if (out) std::memcpy(out, v->data(), sizeof(double) * std::min<size_t>(cap, v->size()));
@@ -1770,9 +1772,14 @@ GemmDesc desc_of(const tatrg_contraction* c) {
                {c->n_ext[2], c->n_sB[2], c->n_sC[2]}, {c->n_ext[3], c->n_sB[3], c->n_sC[3]}});
   g.k = modes({{c->k_ext[0], c->k_sA[0], c->k_sB[0]}, {c->k_ext[1], c->k_sA[1], c->k_sB[1]},
                {c->k_ext[2], c->k_sA[2], c->k_sB[2]}, {c->k_ext[3], c->k_sA[3], c->k_sB[3]}});
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 4; ++i) {
     TATRG_CHECK(c->m_ext[i] >= 1 && c->n_ext[i] >= 1 && c->k_ext[i] >= 1, TATRG_EINVAL,
                 "tatrg_contract: extents must be >= 1");
+    // caller memory is reached from its base pointer only: offsets never go below it
+    TATRG_CHECK(c->m_sA[i] >= 0 && c->m_sC[i] >= 0 && c->n_sB[i] >= 0 && c->n_sC[i] >= 0 &&
+                    c->k_sA[i] >= 0 && c->k_sB[i] >= 0,
+                TATRG_EINVAL, "tatrg_contract: strides must be non-negative");
+  }
   g.alpha = c->alpha;
   g.beta = c->beta;
   return g;
@@ -1802,18 +1809,7 @@ tatrg_status tatrg_contract(const tatrg_contraction* c, int precision, const dou
   return guard(nullptr, [&] {
     TATRG_CHECK(c && A && B && C, TATRG_EINVAL, "tatrg_contract: null argument");
     TATRG_CHECK(precision >= 0 && precision <= 4, TATRG_EINVAL, "tatrg_contract: bad precision");
-    GemmDesc g;
-    g.m = modes({{c->m_ext[0], c->m_sA[0], c->m_sC[0]}, {c->m_ext[1], c->m_sA[1], c->m_sC[1]},
-                 {c->m_ext[2], c->m_sA[2], c->m_sC[2]}, {c->m_ext[3], c->m_sA[3], c->m_sC[3]}});
-    g.n = modes({{c->n_ext[0], c->n_sB[0], c->n_sC[0]}, {c->n_ext[1], c->n_sB[1], c->n_sC[1]},
-                 {c->n_ext[2], c->n_sB[2], c->n_sC[2]}, {c->n_ext[3], c->n_sB[3], c->n_sC[3]}});
-    g.k = modes({{c->k_ext[0], c->k_sA[0], c->k_sB[0]}, {c->k_ext[1], c->k_sA[1], c->k_sB[1]},
-                 {c->k_ext[2], c->k_sA[2], c->k_sB[2]}, {c->k_ext[3], c->k_sA[3], c->k_sB[3]}});
-    for (int i = 0; i < 4; ++i)
-      TATRG_CHECK(c->m_ext[i] >= 1 && c->n_ext[i] >= 1 && c->k_ext[i] >= 1, TATRG_EINVAL,
-                  "tatrg_contract: extents must be >= 1");
-    g.alpha = c->alpha;
-    g.beta = c->beta;
+    const GemmDesc g = desc_of(c);
     Engine e(static_cast<cudaStream_t>(stream));
     e.prec = precision;
     e.gemm(g, A, B, C);

@@ -59,6 +59,11 @@ def test_building_blocks_reject_bad_sizes_before_touching_memory(libpath):
     c = tg._contraction([(4, 4, 4)], [(4, 1, 1)], [(4, 1, 4)], 1.0, 0.0)
     assert L.tatrg_contract(ctypes.byref(c), 5, fake, fake, fake, None) == 1
     assert L.tatrg_contract(ctypes.byref(c), 0, None, fake, fake, None) == 1
+    # a negative stride would reach below the caller's base pointer
+    c = tg._contraction([(4, -4, 4)], [(4, 1, 1)], [(4, 1, 4)], 1.0, 0.0)
+    assert L.tatrg_contract(ctypes.byref(c), 0, fake, fake, fake, None) == 1
+    assert b"non-negative" in L.tatrg_last_error(None)
+    c = tg._contraction([(4, 4, 4)], [(4, 1, 1)], [(4, 1, 4)], 1.0, 0.0)
     # the generated-sketch contraction exists for the split precisions only
     assert L.tatrg_contract_sketch(ctypes.byref(c), 0, fake, 1, 2, 0, fake, None) == 1
     assert b"split precision" in L.tatrg_last_error(None)
