@@ -161,21 +161,29 @@ def blas_threads():
         return int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count()))
 
 
-def oracle_sample(min_seconds=10.0):
-    """Time the FP64 oracle's bond-swap operator on the chi = 48 state: products
-    Mid @ Omega (the first product of the Eq. 1 randomized SVD) with SAMPLE_COLS sketch
-    columns, repeated until min_seconds have passed.  Returns (seconds per RG step scaled by
-    the step's algorithmic flops, description, BLAS threads).  Building the state and the
-    sketch is not timed."""
+def workload_name(chi, r):
+    if (chi, r) == (CHI, R):
+        return WORKLOAD
+    return WORKLOAD.replace("chi=48 r=3", "chi=%d r=%d" % (chi, r)).replace(
+        "legs 48^4, bond 48", "legs %d^4, bond %d" % (chi, chi))
+
+
+def oracle_sample(min_seconds=10.0, chi=CHI, r=R):
+    """Time the FP64 oracle's bond-swap operator on a steady-state state of bond dimension
+    chi (48 for the benchmark): products Mid @ Omega (the first product of the Eq. 1
+    randomized SVD) with SAMPLE_COLS sketch columns, repeated until min_seconds have
+    passed.  Returns (seconds per RG step scaled by the step's algorithmic flops,
+    description, BLAS threads).  Building the state and the sketch is not timed."""
     from oracle import trg
     from paper_2412_14104_gb300 import synth
-    if "op" not in _ORACLE:
-        A, s, B = synth.split_state(7, (CHI,) * 4, CHI)
-        Dk, I, Da = CHI, CHI ** 3, CHI
+    if _ORACLE.get("chi") != chi:
+        A, s, B = synth.split_state(7, (chi,) * 4, chi)
+        Dk, I, Da = chi, chi ** 3, chi
         As = A.reshape(Dk, I, Da) * s[None, None, :]
         Bs = B.reshape(Da, Dk, I) * s[:, None, None]
         _ORACLE["op"] = trg.SwapOp(As, Bs, None)
         _ORACLE["om"] = synth.gaussian_matrix(3, _ORACLE["op"].shape[1], SAMPLE_COLS)
+        _ORACLE["chi"] = chi
     op, om = _ORACLE["op"], _ORACLE["om"]
     reps, dt = 0, 0.0
     while dt < min_seconds or reps == 0:
@@ -183,20 +191,20 @@ def oracle_sample(min_seconds=10.0):
         op.matmul(om)
         dt += time.perf_counter() - t
         reps += 1
-    sample_flops = 4.0 * CHI ** 6 * SAMPLE_COLS * reps
-    per_step = dt * step_flops(CHI, R, Q) / sample_flops
-    desc = ("oracle SwapOp.matmul (Mid @ Omega of the chi=48 bond swap, %d sketch columns) x %d: "
+    sample_flops = 4.0 * chi ** 6 * SAMPLE_COLS * reps
+    per_step = dt * step_flops(chi, r, Q) / sample_flops
+    desc = ("oracle SwapOp.matmul (Mid @ Omega of the chi=%d bond swap, %d sketch columns) x %d: "
             "%.3g flop in %.2f s, scaled to one RG step by its %.3g algorithmic flop" %
-            (SAMPLE_COLS, reps, sample_flops, dt, step_flops(CHI, R, Q)))
+            (chi, SAMPLE_COLS, reps, sample_flops, dt, step_flops(chi, r, Q)))
     return per_step, desc, blas_threads()
 
 
-def one_thread_sample():
+def one_thread_sample(chi=CHI, r=R):
     """The same sample with one BLAS thread, in a child process (the thread count is fixed
     when NumPy loads).  Returns RG steps/s or None."""
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import sys; sys.path.insert(0, %r); import bench; "
-            "print(bench.oracle_sample(min_seconds=1.0)[0])" % ROOT)
+            "print(bench.oracle_sample(min_seconds=1.0, chi=%d, r=%d)[0])" % (ROOT, chi, r))
     try:
         r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
                            timeout=300)
@@ -205,22 +213,23 @@ def one_thread_sample():
         return None
 
 
-def cpu_baseline_record(min_seconds):
-    per, desc, threads = oracle_sample(min_seconds=min_seconds)
+def cpu_baseline_record(min_seconds, chi=CHI, r=R):
+    per, desc, threads = oracle_sample(min_seconds=min_seconds, chi=chi, r=r)
     return {"value": 1.0 / per, "unit": "RG steps/s", "cores": threads, "kind": "oracle",
             "sample": desc, "cpu_model": cpu_model(), "nproc": os.cpu_count(),
-            "value_1_thread": one_thread_sample()}
+            "value_1_thread": one_thread_sample(chi, r)}
 
 
 def run_reference(args, world, rank):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(min_seconds=0.0)
+        oracle_sample(min_seconds=0.0, chi=args.chi, r=args.r)
     times = []
     desc, threads = "", os.cpu_count()
     for _ in range(args.steps):
-        per_step, desc, threads = oracle_sample(min_seconds=args.sample_seconds / max(args.steps, 1))
+        per_step, desc, threads = oracle_sample(min_seconds=args.sample_seconds / max(args.steps, 1),
+                                                chi=args.chi, r=args.r)
         times.append(per_step)
     per = sum(times) / len(times)
     value = 1.0 / per
@@ -229,7 +238,7 @@ def run_reference(args, world, rank):
         "value": value, "unit": "RG steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "chi": CHI, "r": R, "q": Q},
+        "config": {"workload": workload_name(args.chi, args.r), "chi": args.chi, "r": args.r, "q": Q},
         "cpu_baseline": {"value": value, "unit": "RG steps/s", "cores": threads, "kind": "oracle",
                          "sample": desc + "; each timed step is one such sample, ms_per_step is "
                          "the extrapolated step time", "cpu_model": cpu_model(),
@@ -738,8 +747,7 @@ def run_ours(args, world, rank, local):
 
     if rank != 0:
         return
-    workload = WORKLOAD if (chi, r) == (CHI, R) else WORKLOAD.replace(
-        "chi=48 r=3", "chi=%d r=%d" % (chi, r)).replace("legs 48^4, bond 48", "legs %d^4, bond %d" % (chi, chi))
+    workload = workload_name(chi, r)
     line = {
         "metric": METRIC,
         "value": value, "unit": "RG steps/s", "n_gpus": world, "steps": args.steps,
@@ -800,7 +808,7 @@ def run_ours(args, world, rank, local):
         line["stored_runs"] = dict(stored, note="whole-run measurements of the other configurations, "
                                                 "written by the commands named in each (not re-run here)")
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_record(10.0)
+        line["cpu_baseline"] = cpu_baseline_record(10.0, chi, r)
     print(json.dumps(line), flush=True)
 
 

@@ -9,8 +9,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_prints_one_contract_line():
+    # chi = 16 keeps the oracle state small (the benchmark's chi = 48 state takes minutes
+    # to build); the line's keys do not depend on it
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0", "--sample-seconds", "1"],
+                          "--steps", "1", "--warmup", "0", "--sample-seconds", "1", "--chi", "16",
+                          "--r", "2"],
                          capture_output=True, text=True, timeout=1200, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.strip().startswith("{")]
@@ -22,7 +25,7 @@ def test_reference_arm_prints_one_contract_line():
         assert key in d, key
     assert d["impl"] == "reference" and d["unit"] == "RG steps/s" and d["value"] > 0
     assert d["higher_is_better"] is True and d["vs_baseline"] is None
-    assert "workload" in d["config"]
+    assert "chi=16 r=2" in d["config"]["workload"] and d["config"]["chi"] == 16
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     e = d["e2e"]
