@@ -402,6 +402,24 @@ def test_canonical_basis_is_rotation_invariant():
     assert np.array_equal(F1, C3)
 
 
+def test_split_multiplet_gap_leaves_the_chi24_run_unchanged():
+    """The multiplet gap of the float-grade split steps (tau = 1e-6) against the float64
+    one (1e-10) on the stored chi = 24, 40-step oracle runs (tests/golden/make_golden.py,
+    c2_chi24 and c2_chi24_tau6 with tau = 1e-6 from step 1): every ln c_k, every kept
+    dimension and ln Z / V are identical, so on this run the wider gap changes no cut and a
+    split-precision free-energy difference there is rounding alone."""
+    import json
+    gold = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    with open(os.path.join(gold, "oracle_c2_chi24.json")) as f:
+        a = json.load(f)
+    with open(os.path.join(gold, "oracle_c2_chi24_tau6.json")) as f:
+        b = json.load(f)
+    assert b["config"]["split_tau"] == 1e-6 and b["config"]["split_from_step"] == 1
+    assert {k: v for k, v in a["config"].items() if k not in ("split_tau", "split_from_step")} == \
+        {k: v for k, v in b["config"].items() if k not in ("split_tau", "split_from_step")}
+    assert a["lnc"] == b["lnc"] and a["dims"] == b["dims"] and a["lnz"] == b["lnz"]
+
+
 def test_multiplet_cut_never_splits():
     vals = np.array([5.0, 4.0, 3.0, 3.0, 3.0, 2.0, 1.0])
     assert rla.multiplet_cut(vals, 3, 1e-10) == 2
